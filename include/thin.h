@@ -1,0 +1,179 @@
+/*
+ * thin.h -- C-ABI of the GB300 grayscale lambda-thinning library (libthin.so).
+ *
+ * The operation: grayscale lambda-thinning under (8,4)-adjacency.  Every
+ * lambda-destructible point (Sec. 2.1: a destructible point, or a
+ * k-divergent point with at least k-1 lower components c such that
+ * F(x) - F^-(c) <= lambda) is lowered to alpha^-(x, F), the largest value among
+ * its strictly lower 8-neighbours (Sec. 2.1), repeatedly until no such point
+ * remains (the lowering loop of Sec. 2.2, with lambda-destructible points in
+ * place of lambda-deletable, non-lambda-end ones).
+ *
+ * The order of lowering is fixed so that the result is unique: a 2x2-parity
+ * subfield schedule.  Phase g (a global phase index, 0, 1, 2, ...) visits the
+ * interior points with 2*(y & 1) + (x & 1) == g mod 4; such points are
+ * pairwise not 8-adjacent, so a phase equals any sequential order over its
+ * points.  Within its phase a point is lowered until it is no longer
+ * lambda-destructible.  The run stops once four consecutive phases change
+ * nothing.  Border pixels (x = 0, x = w-1, y = 0, y = h-1) are read as
+ * neighbours and never written.
+ *
+ * Layout: an image is h rows of w pixels, row-major, rows `pitch_bytes` apart;
+ * pixel (x, y) is column x of row y.  u8 images hold uint8_t, u16 images
+ * uint16_t (the full 0..65535 range is allowed).
+ *
+ * Ownership: image memory belongs to the caller, who keeps it alive until the
+ * work queued on `stream` has finished.  Calls are asynchronous on `stream`
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream) unless a
+ * stats pointer is given: then the call waits for the stream and fills the
+ * stats before returning.  Scratch memory is taken from, and returned to,
+ * the CUDA stream-ordered allocator on the same stream.
+ *
+ * Errors: every entry point returns THIN_OK (0) or a negative THIN_ERR_* code
+ * and leaves the image untouched when it rejects its arguments.  Errors found
+ * on the device (a bounded wait that ran out) are reported in stats.status.
+ */
+#ifndef THIN_H
+#define THIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THIN_OK 0
+#define THIN_ERR_ARG (-1)           /* bad pointer, size, pitch, dtype, lambda or option */
+#define THIN_ERR_UNSUPPORTED (-2)   /* (4,8)-adjacency, or an option this build lacks */
+#define THIN_ERR_OOM (-3)           /* scratch allocation failed */
+#define THIN_ERR_NOT_CONVERGED (-4) /* stopped by max_phases before stability */
+#define THIN_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
+#define THIN_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define THIN_EAGAIN (-7)            /* serving: over the memory budget and the queue is full */
+
+typedef enum { THIN_U8 = 0, THIN_U16 = 1 } thin_dtype;
+typedef enum { THIN_ADJ_8_4 = 0, THIN_ADJ_4_8 = 1 } thin_adj;
+
+/* Reading of F^-(c) in the lambda rule (Sec. 2.1 leaves F^- undefined):
+ * THIN_RULE_MAX takes the largest value of F over the component c (default),
+ * THIN_RULE_MIN the smallest. */
+typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
+
+/* Kernel family: AUTO picks the tiled kernel; NAIVE runs one launch per phase
+ * straight from global memory (the reference slice). */
+typedef enum { THIN_KERNEL_AUTO = 0, THIN_KERNEL_NAIVE = 1, THIN_KERNEL_TILED = 2 } thin_kernel;
+
+typedef struct {
+    int32_t rule;        /* thin_rule */
+    int32_t kernel;      /* thin_kernel */
+    int32_t tile_w;      /* tile width in pixels, 0 = default; multiple of 16, 16..224 */
+    int32_t tile_h;      /* tile height in pixels, 0 = default; 8..240 */
+    int32_t halo;        /* phases per tile visit = halo width, 0 = default; 1..8 */
+    int32_t reserved;
+    int64_t start_phase; /* global phase index of the first phase (resume), >= 0 */
+    int64_t max_phases;  /* stop after this many phases; < 0 = run to stability */
+} thin_options;
+
+typedef struct {
+    int32_t status;            /* THIN_OK, THIN_ERR_NOT_CONVERGED or THIN_ERR_TIMEOUT */
+    int32_t converged;         /* 1 if a quiet stretch of four phases was seen */
+    int64_t phases;            /* phases run by this call */
+    int64_t lowered;           /* lowering steps F(x) := alpha^- performed */
+    int64_t last_change_phase; /* global index of the last phase that lowered a point; -1 if none */
+    int64_t end_phase;         /* global phase index to resume from */
+    int64_t tiles_visited;     /* tile visits of the tiled kernel (0 for NAIVE) */
+    int64_t steps;             /* tile steps (tiled) or rounds of four phases (naive) */
+} thin_stats;
+
+/* Fills *opt with the defaults (rule MAX, AUTO kernel, default tiles, phase 0, no cap). */
+void thin_default_options(thin_options *opt);
+
+/*
+ * Lambda-thin one image in place (Sec. 2.1-2.2).
+ *   img_dev      device pointer to pixel (0, 0); u8 images need no alignment,
+ *                u16 images 2-byte alignment
+ *   w, h         width and height in pixels; w <= 0 or h <= 0 with w, h >= 0
+ *                is an empty image (no-op); images narrower or lower than 3
+ *                pixels have no interior point and are left unchanged
+ *   pitch_bytes  distance between rows, >= w * element size
+ *   dt           THIN_U8 or THIN_U16
+ *   lambda       the contrast parameter, an integer >= 0 (Sec. 2.1)
+ *   adj          THIN_ADJ_8_4; THIN_ADJ_4_8 returns THIN_ERR_UNSUPPORTED
+ *   stream       cudaStream_t as void*
+ *   opt          options, NULL = defaults
+ *   out          stats, NULL = fully asynchronous call
+ */
+int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
+             thin_adj adj, void *stream, const thin_options *opt, thin_stats *out);
+
+/* One image of a batch. */
+typedef struct {
+    void *img_dev;      /* device pointer, caller-owned, thinned in place */
+    int32_t w, h;       /* width, height in pixels */
+    size_t pitch;       /* row pitch in bytes */
+    int32_t dtype;      /* thin_dtype */
+    uint32_t lambda;    /* per-image lambda */
+} thin_job;
+
+/*
+ * Lambda-thin n independent images of any sizes, dtypes and lambdas in one
+ * device-driven run (a CUDA graph whose body loops on the device until every
+ * image is stable).  Each image gets exactly the result thin_run gives it
+ * alone.  opt applies to every image (its start_phase too).  out: array of n
+ * stats or NULL.  n == 0 is a no-op.
+ */
+int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const thin_options *opt,
+               thin_stats *out);
+
+/*
+ * The 256-entry point-test table the kernels use, written to out[256]
+ * (host memory, no GPU needed).  Entry m describes a point whose strictly
+ * lower neighbours form the ring mask m (bit i = neighbour i in the order E,
+ * NE, N, NW, W, SW, S, SE):
+ *   bits 0-2   T+  = number of 8-components of the other neighbours (Sec. 2.1)
+ *   bits 3-5   T-- = number of 4-components of the lower neighbours holding a
+ *              4-neighbour of x (Sec. 2.1, complement side of (8,4))
+ *   bits 6-29  3-bit field per neighbour i at bit 6+3i: 1 + the index of its
+ *              counted T-- component, 0 if none
+ *   bit 30     destructible (T+ == 1 and T-- == 1)
+ *   bit 31     k-divergent (T-- >= 2)
+ */
+void thin_point_table(uint32_t out[256]);
+
+/* Library version string. */
+const char *thin_version(void);
+
+/* ----------------------------------------------------------------------
+ * Serving: continuous batching under a device-memory budget.
+ * A server owns a worker thread and a CUDA stream.  submit copies the host
+ * image into a device slot and returns at once with a ticket; the worker
+ * admits queued requests while the slots and the byte budget allow, runs the
+ * active set with the batch engine, and retires each image as soon as it is
+ * stable; poll copies a finished image back to the host.
+ * -------------------------------------------------------------------- */
+typedef struct thin_server thin_server;
+
+/* device_budget_bytes: cap on device bytes held by admitted requests (image
+ * plus scratch); max_slots: cap on requests in flight; queue_cap: cap on
+ * requests waiting for admission (submit returns THIN_EAGAIN beyond it). */
+int thin_serve_create(size_t device_budget_bytes, int max_slots, int queue_cap, thin_server **out);
+
+/* Queue one host image (copied before return).  *ticket identifies it. */
+int thin_serve_submit(thin_server *s, const void *host_img, int w, int h, size_t pitch,
+                      thin_dtype dt, uint32_t lambda, uint64_t *ticket);
+
+/* Non-blocking: *done = 1 and the result copied to host_out (out_pitch bytes
+ * per row) once the request is finished; the ticket is then retired.
+ * *done = 0 while it is queued or running.  stats may be NULL. */
+int thin_serve_poll(thin_server *s, uint64_t ticket, void *host_out, size_t out_pitch, int *done,
+                    thin_stats *stats);
+
+/* Stops the worker (finishing admitted work) and frees everything. */
+int thin_serve_destroy(thin_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THIN_H */

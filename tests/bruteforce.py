@@ -1,0 +1,111 @@
+"""Brute-force references written in the tests, independent of the oracle's C code.
+
+They restate the definitions of Sec. 2.1 with scipy's connected-component
+labelling instead of the oracle's breadth-first search, and re-run the
+subfield schedule in plain Python.  Only usable on tiny images.
+"""
+import numpy as np
+from scipy import ndimage
+
+EIGHT = np.ones((3, 3), dtype=int)
+FOUR = np.array([[0, 1, 0], [1, 1, 1], [0, 1, 0]])
+# ring order E, NE, N, NW, W, SW, S, SE as (row, col) in a 3x3 grid
+RING_RC = [(1, 2), (0, 2), (0, 1), (0, 0), (1, 0), (2, 0), (2, 1), (2, 2)]
+FOUR_NEIGHBOURS_RC = {(0, 1), (1, 0), (1, 2), (2, 1)}
+
+
+def ring_values(grid):
+    g = np.asarray(grid)
+    return [int(g[r, c]) for r, c in RING_RC]
+
+
+def grid_from_ring(center, nb):
+    g = np.zeros((3, 3), dtype=np.int64)
+    g[1, 1] = center
+    for (r, c), v in zip(RING_RC, nb):
+        g[r, c] = v
+    return g
+
+
+def local_numbers(grid):
+    """(T+, T--, list of lower components as sets of (r, c)) by scipy labelling."""
+    g = np.asarray(grid, dtype=np.int64)
+    c = g[1, 1]
+    upper = (g >= c)
+    upper[1, 1] = False
+    lower = (g < c)
+    lower[1, 1] = False
+    lu, nu = ndimage.label(upper, structure=EIGHT)
+    ll, nl = ndimage.label(lower, structure=FOUR)
+    comps = []
+    for lab in range(1, nl + 1):
+        pts = set(zip(*np.nonzero(ll == lab)))
+        if pts & FOUR_NEIGHBOURS_RC:
+            comps.append(pts)
+    return nu, len(comps), comps
+
+
+def point_step(grid, lam, rule):
+    """(lambda_destructible, alpha) of the centre of a 3x3 grid, from the definitions."""
+    g = np.asarray(grid, dtype=np.int64)
+    c = int(g[1, 1])
+    tplus, tminus, comps = local_numbers(g)
+    lower = [(r, cc) for r in range(3) for cc in range(3) if (r, cc) != (1, 1) and g[r, cc] < c]
+    if not lower:
+        return False, c
+    alpha = max(int(g[p]) for p in lower)
+    if tplus == 1 and tminus == 1:
+        return True, alpha
+    if tminus > 1:
+        f = max if rule == 0 else min
+        ok = sum(1 for comp in comps if c - f(int(g[p]) for p in comp) <= lam)
+        if ok >= tminus - 1:
+            return True, alpha
+    return False, alpha
+
+
+def components(mask, structure):
+    return ndimage.label(mask, structure=structure)[1]
+
+
+def global_destructible(img, x, y):
+    """Removing (x, y) from F_k, k = F(x, y), keeps #8-components of F_k and
+    #4-components of its complement (scipy labelling on the finite grid)."""
+    a = np.asarray(img, dtype=np.int64)
+    k = a[y, x]
+    X = a >= k
+    Xm = X.copy()
+    Xm[y, x] = False
+    return (components(X, EIGHT) == components(Xm, EIGHT) and
+            components(~X, FOUR) == components(~Xm, FOUR))
+
+
+def schedule(img, lam, rule=0, use_global=False, max_rounds=10000):
+    """Subfield-schedule thinning in plain Python: phases 0,1,2,3,... visit the
+    interior points of parity 2(y&1)+(x&1); each is lowered to alpha^- while it
+    is lambda-destructible (use_global: destructible by global component
+    counts, lambda = 0 only).  Stops after a round with no change."""
+    a = np.asarray(img, dtype=np.int64).copy()
+    h, w = a.shape
+    for _ in range(max_rounds):
+        changed = False
+        for p in range(4):
+            for y in range(1, h - 1):
+                for x in range(1, w - 1):
+                    if 2 * (y & 1) + (x & 1) != p:
+                        continue
+                    while True:
+                        g = a[y - 1:y + 2, x - 1:x + 2]
+                        if use_global:
+                            lower = [int(v) for (r, c), v in np.ndenumerate(g) if (r, c) != (1, 1) and v < g[1, 1]]
+                            ok = bool(lower) and global_destructible(a, x, y)
+                            alpha = max(lower) if lower else int(g[1, 1])
+                        else:
+                            ok, alpha = point_step(g, lam, rule)
+                        if not ok:
+                            break
+                        a[y, x] = alpha
+                        changed = True
+        if not changed:
+            return a
+    raise RuntimeError("no convergence")

@@ -1,0 +1,287 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: the references are hand-worked
+cases (tests/golden), a textbook identity of (8,4) digital topology, global
+component counts by scipy labelling (brute force), closed forms of the lambda
+rule, and invariants of the operator (Sec. 2.1-2.2).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_09180_gb300.synth import uniform_noise_image, value_noise_image
+from tests import bruteforce as bf
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "point_cases.json")
+RULES = {"max": oracle.RULE_MAX, "min": oracle.RULE_MIN}
+
+
+def lower_mask(grid):
+    g = np.asarray(grid)
+    nb = bf.ring_values(g)
+    return sum(1 << i for i, v in enumerate(nb) if v < g[1, 1])
+
+
+# ---------------------------------------------------------------- point test
+
+def test_golden_point_cases():
+    cases = json.load(open(GOLDEN))["cases"]
+    assert len(cases) >= 8
+    for c in cases:
+        g = np.array(c["grid"])
+        tp, tm, _ = oracle.mask_numbers(lower_mask(g))
+        assert (tp, tm) == (c["tplus"], c["tminus"]), c["name"]
+        assert (tp == 1 and tm == 1) == c["destructible"], c["name"]
+        for chk in c["checks"]:
+            ok, alpha = oracle.lambda_destructible(bf.ring_values(g), g[1, 1], chk["lam"], RULES[chk["rule"]])
+            assert ok == chk["first"], (c["name"], chk)
+            if ok:
+                assert alpha == c["alpha"], c["name"]
+            out, st = oracle.thin(g.astype(np.int32), chk["lam"], RULES[chk["rule"]])
+            assert out[1, 1] == chk["final"], (c["name"], chk)
+            # the border of a 3x3 image is never written
+            mask = np.ones((3, 3), bool)
+            mask[1, 1] = False
+            assert (out[mask] == g[mask]).all()
+
+
+def test_84_identity_all_masks():
+    """(8,4) in 2-D: T+ = T-- except at a 4-interior point (no strictly lower
+    4-neighbour, lower corners allowed: T+ = 1, T-- = 0) and an isolated point
+    (all eight lower: T+ = 0, T-- = 1)."""
+    four = 0b01010101  # E, N, W, S
+    for m in range(256):
+        tp, tm, _ = oracle.mask_numbers(m)
+        if m & four == 0:
+            assert (tp, tm) == (1, 0)
+        elif m == 255:
+            assert (tp, tm) == (0, 1)
+        else:
+            assert tp == tm, m
+        assert 0 <= tp <= 4 and 0 <= tm <= 4
+
+
+def test_all_masks_against_scipy_labelling():
+    for m in range(256):
+        nb = [0 if (m >> i) & 1 else 2 for i in range(8)]
+        g = bf.grid_from_ring(1, nb)
+        tp_ref, tm_ref, comps = bf.local_numbers(g)
+        tp, tm, lab = oracle.mask_numbers(m)
+        assert (tp, tm) == (tp_ref, tm_ref), m
+        # same partition of the lower neighbours into counted components
+        ref_part = {frozenset(c) for c in comps}
+        got = {}
+        for i, l in enumerate(lab):
+            if l >= 0:
+                got.setdefault(l, set()).add(bf.RING_RC[i])
+        assert {frozenset(s) for s in got.values()} == ref_part, m
+
+
+def test_tplusplus_matches_labelling():
+    for m in range(256):
+        g = bf.grid_from_ring(1, [2 if (m >> i) & 1 else 1 for i in range(8)])
+        up = g > 1
+        up[1, 1] = False
+        assert oracle.tplusplus(m) == bf.components(up, bf.EIGHT)
+
+
+def test_simple_count_among_masks():
+    """Number of ring configurations with T+ = 1 and T-- = 1 (simple points of
+    a binary set under (8,4)), cross-checked against the global brute force."""
+    simple = [m for m in range(256) if oracle.mask_numbers(m)[:2] == (1, 1)]
+    glob = []
+    for m in range(256):
+        img = np.full((5, 5), 1, dtype=np.int32)
+        g = bf.grid_from_ring(1, [0 if (m >> i) & 1 else 1 for i in range(8)])
+        img[1:4, 1:4] = g
+        # outer ring at 1: the lower neighbours (0) only touch each other through x
+        if bf.global_destructible(img, 2, 2) and m != 0:
+            glob.append(m)
+    assert simple == glob
+
+
+@pytest.mark.parametrize("outer", ["zeros", "ones", "twos", "random"])
+def test_local_equals_global_all_masks(outer):
+    rng = np.random.default_rng(5)
+    for m in range(256):
+        img = {"zeros": np.zeros((5, 5)), "ones": np.ones((5, 5)), "twos": np.full((5, 5), 2),
+               "random": rng.integers(0, 3, (5, 5))}[outer].astype(np.int32)
+        img[1:4, 1:4] = bf.grid_from_ring(1, [0 if (m >> i) & 1 else 2 for i in range(8)])
+        local, _ = oracle.lambda_destructible(bf.ring_values(img[1:4, 1:4]), 1, 0)
+        assert local == oracle.global_destructible(img, 2, 2) == bf.global_destructible(img, 2, 2), (m, outer)
+
+
+@pytest.mark.parametrize("shape,levels,count", [((4, 4), 3, 3000), ((5, 5), 3, 1500), ((8, 8), 4, 150)])
+def test_local_equals_global_random_images(shape, levels, count):
+    rng = np.random.default_rng(11 + shape[0])
+    h, w = shape
+    for _ in range(count):
+        img = rng.integers(0, levels, shape).astype(np.int32)
+        for y in range(1, h - 1):
+            for x in range(1, w - 1):
+                local, _ = oracle.lambda_destructible(bf.ring_values(img[y - 1:y + 2, x - 1:x + 2]), img[y, x], 0)
+                assert local == oracle.global_destructible(img, x, y), (img, x, y)
+                if count <= 150:
+                    assert local == bf.global_destructible(img, x, y)
+
+
+def test_lambda_rule_against_reference():
+    rng = np.random.default_rng(3)
+    for _ in range(4000):
+        g = rng.integers(0, 7, (3, 3))
+        nb = bf.ring_values(g)
+        for lam in (0, 1, 2, 4):
+            for rule in (0, 1):
+                got = oracle.lambda_destructible(nb, g[1, 1], lam, rule)
+                ref = bf.point_step(g, lam, rule)
+                assert got[0] == ref[0], (g, lam, rule)
+                if got[0]:
+                    assert got[1] == ref[1]
+
+
+def test_lambda_closed_forms():
+    rng = np.random.default_rng(8)
+    for _ in range(3000):
+        g = rng.integers(0, 9, (3, 3))
+        nb, c = bf.ring_values(g), int(g[1, 1])
+        d0 = oracle.lambda_destructible(nb, c, 0)[0]
+        tp, tm, _ = oracle.mask_numbers(lower_mask(g))
+        # lambda = 0: components are strictly lower, so only destructible points qualify
+        assert d0 == (tp == 1 and tm == 1)
+        prev = d0
+        for lam in range(1, 10):
+            cur = oracle.lambda_destructible(nb, c, lam)[0]
+            assert cur >= prev  # monotone in lambda
+            prev = cur
+        ok, alpha = oracle.lambda_destructible(nb, c, 9)
+        if ok:
+            assert alpha == max(v for v in nb if v < c) < c
+        if tm >= 2 and prev:
+            # a k-divergent point at lambda >= its full contrast is always lambda-destructible
+            assert oracle.lambda_destructible(nb, c, c)[0]
+        # constant-valued components: R1 and R2 agree
+        if len({v for v in nb if v < c}) <= 1:
+            for lam in range(0, 10):
+                assert oracle.lambda_destructible(nb, c, lam, 0)[0] == oracle.lambda_destructible(nb, c, lam, 1)[0]
+
+
+# ---------------------------------------------------------------- schedule
+
+@pytest.mark.parametrize("lam,rule", [(0, 0), (1, 0), (3, 0), (2, 1)])
+def test_schedule_against_python_reference(lam, rule):
+    rng = np.random.default_rng(100 + lam + 10 * rule)
+    for _ in range(12):
+        h, w = int(rng.integers(3, 9)), int(rng.integers(3, 10))
+        img = rng.integers(0, 5, (h, w)).astype(np.int32)
+        out, st = oracle.thin(img, lam, rule)
+        assert np.array_equal(out, bf.schedule(img, lam, rule)), img
+        assert st["converged"] == 1
+
+
+def test_schedule_lambda0_against_global_brute_force():
+    """At lambda = 0 each lowering is decided by global component counts of the
+    threshold sections: the local point test must lead to the same image."""
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        h, w = int(rng.integers(4, 8)), int(rng.integers(4, 8))
+        img = rng.integers(0, 4, (h, w)).astype(np.int32)
+        out, _ = oracle.thin(img, 0)
+        assert np.array_equal(out, bf.schedule(img, 0, use_global=True)), img
+
+
+def test_binary_reduces_to_simple_point_thinning():
+    """A {0,1} image at lambda = 0 is binary thinning by deletion of simple
+    points in the subfield order; deletion decided by global counts."""
+    rng = np.random.default_rng(4)
+    blob = np.zeros((14, 14), np.int32)
+    for _ in range(6):
+        y, x, r = rng.integers(2, 12), rng.integers(2, 12), rng.integers(1, 4)
+        yy, xx = np.mgrid[:14, :14]
+        blob[(yy - y) ** 2 + (xx - x) ** 2 <= r * r] = 1
+    blob[0, :] = blob[-1, :] = blob[:, 0] = blob[:, -1] = 0
+    out, _ = oracle.thin(blob, 0)
+    ref = bf.schedule(blob, 0, use_global=True)
+    assert np.array_equal(out, ref)
+    assert set(np.unique(out)) <= {0, 1}
+    assert (out <= blob).all()
+
+
+def _invariants(img, out, lam):
+    assert out.shape == img.shape and out.dtype == img.dtype
+    assert (out <= img).all()
+    assert oracle.count_lambda_destructible(out, lam) == 0
+    b = np.ones(img.shape, bool)
+    b[1:-1, 1:-1] = False
+    assert (out[b] == img[b]).all()
+
+
+@pytest.mark.parametrize("lam", [0, 5, 20])
+def test_invariants_on_generator_images(lam):
+    img = value_noise_image(40, 56, "u8", seed=7)
+    out, st = oracle.thin(img, lam)
+    _invariants(img, out, lam)
+    assert st["converged"] == 1 and st["lowered"] > 0
+    if lam == 0:
+        assert oracle.level_topology(img) == oracle.level_topology(out, levels=sorted(oracle.level_topology(img)))
+
+
+@pytest.mark.parametrize("variant", ["queue", "minvalue"])
+@pytest.mark.parametrize("lam", [0, 6])
+def test_other_orders_same_invariants(variant, lam):
+    img = value_noise_image(32, 48, "u8", seed=9)
+    f = oracle.thin_queue if variant == "queue" else oracle.thin_minvalue
+    out, n = f(img, lam)
+    _invariants(img, out, lam)
+    sched, _ = oracle.thin(img, lam)
+    if lam == 0:
+        levels = sorted(oracle.level_topology(img))
+        assert oracle.level_topology(out, levels) == oracle.level_topology(sched, levels) == oracle.level_topology(img, levels)
+
+
+def test_constant_image_and_peak_unchanged():
+    c = np.full((9, 11), 77, np.uint8)
+    out, st = oracle.thin(c, 30)
+    assert np.array_equal(out, c) and st["lowered"] == 0 and st["rounds"] == 1
+    assert st["last_change_phase"] == -1
+    p = np.full((9, 9), 10, np.uint8)
+    p[4, 4] = 200
+    out, st = oracle.thin(p, 0)
+    assert np.array_equal(out, p)
+
+
+@pytest.mark.parametrize("d,lam", [(3, 2), (3, 3), (5, 4), (5, 5), (5, 9)])
+def test_flat_basins_merge_iff_depth_le_lambda(d, lam):
+    H = 10
+    img = np.full((15, 21), H, np.int32)
+    img[4:11, 3:10] = H - d   # basin 1
+    img[4:11, 11:18] = H - d  # basin 2, column 10 is a 1-px ridge
+    out, _ = oracle.thin(img, lam)
+    n_low = bf.components(out < H, bf.FOUR)
+    assert n_low == (1 if d <= lam else 2)
+    for rule in (0, 1):  # constant basins: the F^- reading does not matter
+        assert np.array_equal(oracle.thin(img, lam, rule)[0], out)
+
+
+def test_resume_equals_uninterrupted():
+    img = value_noise_image(33, 47, "u8", seed=3)
+    full, st = oracle.thin(img, 5)
+    for k in (1, 3, 4, 9, 22):
+        part, s1 = oracle.thin(img, 5, max_phases=k)
+        assert s1["capped"] and s1["end_phase"] == k
+        rest, s2 = oracle.thin(part, 5, start_phase=k)
+        assert np.array_equal(rest, full)
+        assert s1["lowered"] + s2["lowered"] == st["lowered"]
+
+
+def test_u16_and_tiny_shapes():
+    img = uniform_noise_image(12, 13, "u16", seed=2, vmax=65535)
+    out, _ = oracle.thin(img, 1000)
+    _invariants(img, out, 1000)
+    for shape in [(0, 0), (1, 5), (2, 2), (5, 2), (3, 3)]:
+        a = np.arange(int(np.prod(shape)), dtype=np.uint8).reshape(shape)
+        o, st = oracle.thin(a, 0) if a.size else (a, None)
+        if a.size and min(shape) < 3:
+            assert np.array_equal(o, a)
