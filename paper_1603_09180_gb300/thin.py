@@ -1,0 +1,197 @@
+"""Python binding of libthin.so (ctypes).  Argument marshalling only.
+
+Every step of lambda-thinning runs in the library's CUDA kernels; PyTorch
+supplies device memory and the current stream.  There is no CPU fallback: if
+the library is missing or fails to load, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libthin.so")
+
+THIN_OK = 0
+THIN_ERR_ARG = -1
+THIN_ERR_UNSUPPORTED = -2
+THIN_ERR_OOM = -3
+THIN_ERR_NOT_CONVERGED = -4
+THIN_ERR_TIMEOUT = -5
+THIN_ERR_CUDA = -6
+THIN_EAGAIN = -7
+ERRORS = {THIN_ERR_ARG: "bad argument", THIN_ERR_UNSUPPORTED: "unsupported", THIN_ERR_OOM: "out of memory",
+          THIN_ERR_NOT_CONVERGED: "not converged", THIN_ERR_TIMEOUT: "device wait timed out",
+          THIN_ERR_CUDA: "CUDA error", THIN_EAGAIN: "over budget, try again"}
+
+U8, U16 = 0, 1
+ADJ_8_4, ADJ_4_8 = 0, 1
+RULE_MAX, RULE_MIN = 0, 1
+KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2
+
+
+class ThinError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__("%s: %s (%d)" % (what, ERRORS.get(code, "error"), code))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32), ("halo", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("start_phase", ctypes.c_int64), ("max_phases", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("converged", ctypes.c_int32), ("phases", ctypes.c_int64),
+                ("lowered", ctypes.c_int64), ("last_change_phase", ctypes.c_int64), ("end_phase", ctypes.c_int64),
+                ("tiles_visited", ctypes.c_int64), ("steps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("img_dev", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("pitch", ctypes.c_size_t), ("dtype", ctypes.c_int32), ("lam", ctypes.c_uint32)]
+
+
+EXPORTS = ["thin_default_options", "thin_run", "thin_batch", "thin_point_table", "thin_version",
+           "thin_serve_create", "thin_serve_submit", "thin_serve_poll", "thin_serve_destroy"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libthin.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libthin.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, u32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
+    lib.thin_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.thin_default_options.restype = None
+    lib.thin_run.argtypes = [vp, i32, i32, sz, i32, u32, i32, vp, ctypes.POINTER(Options), ctypes.POINTER(Stats)]
+    lib.thin_run.restype = i32
+    lib.thin_batch.argtypes = [ctypes.POINTER(Job), i32, i32, vp, ctypes.POINTER(Options), ctypes.POINTER(Stats)]
+    lib.thin_batch.restype = i32
+    lib.thin_point_table.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+    lib.thin_point_table.restype = None
+    lib.thin_version.restype = ctypes.c_char_p
+    lib.thin_serve_create.argtypes = [sz, i32, i32, ctypes.POINTER(vp)]
+    lib.thin_serve_create.restype = i32
+    lib.thin_serve_submit.argtypes = [vp, vp, i32, i32, sz, i32, u32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.thin_serve_submit.restype = i32
+    lib.thin_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, sz, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Stats)]
+    lib.thin_serve_poll.restype = i32
+    lib.thin_serve_destroy.argtypes = [vp]
+    lib.thin_serve_destroy.restype = i32
+    _lib = lib
+    return lib
+
+
+def options(rule=RULE_MAX, kernel=KERNEL_AUTO, tile=None, halo=0, start_phase=0, max_phases=-1, debug=0):
+    o = Options()
+    load().thin_default_options(ctypes.byref(o))
+    o.rule = {"max": RULE_MAX, "min": RULE_MIN}.get(rule, rule)
+    o.kernel = {"auto": KERNEL_AUTO, "naive": KERNEL_NAIVE, "tiled": KERNEL_TILED}.get(kernel, kernel)
+    if tile is not None:
+        o.tile_w, o.tile_h = (tile, tile) if isinstance(tile, int) else tile
+    o.halo = halo or 0
+    o.start_phase = start_phase
+    o.max_phases = max_phases
+    o.reserved = debug
+    return o
+
+
+def point_table():
+    out = (ctypes.c_uint32 * 256)()
+    load().thin_point_table(out)
+    return list(out)
+
+
+def version() -> str:
+    return load().thin_version().decode()
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.uint8:
+        return U8
+    if t.dtype == torch.uint16:
+        return U16
+    raise TypeError("image must be torch.uint8 or torch.uint16")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def run(img, lam: int, *, rule="max", kernel="auto", tile=None, halo=0, start_phase=0, max_phases=-1,
+        stream=None, stats=True, check=True, debug=0):
+    """Lambda-thin a CUDA tensor (H x W, uint8/uint16, unit column stride) in place.
+
+    Returns the stats dict (stats=True waits for the stream), else None."""
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dim() != 2 or (img.numel() and img.stride(1) != 1):
+        raise ValueError("image must be 2-D with unit column stride")
+    h, w = img.shape
+    es = img.element_size()
+    pitch = img.stride(0) * es if h > 1 else w * es
+    st = Stats()
+    o = options(rule, kernel, tile, halo, start_phase, max_phases, debug)
+    rc = load().thin_run(ctypes.c_void_p(img.data_ptr() if img.numel() else 0), w, h, pitch, _dtype_code(img),
+                         int(lam), ADJ_8_4, _stream_ptr(stream), ctypes.byref(o),
+                         ctypes.byref(st) if stats else None)
+    if check and rc not in (THIN_OK, THIN_ERR_NOT_CONVERGED):
+        raise ThinError(rc, "thin_run")
+    if stats:
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+    return rc
+
+
+def run_raw(ptr: int, w: int, h: int, pitch: int, dtype: int, lam: int, adj: int = ADJ_8_4, stream_ptr: int = 0,
+            opts: Options | None = None, want_stats: bool = True):
+    """Direct C-ABI call with plain integers (device pointer as int).  Returns (rc, stats dict)."""
+    st = Stats()
+    rc = load().thin_run(ctypes.c_void_p(ptr), w, h, pitch, dtype, lam, adj, ctypes.c_void_p(stream_ptr),
+                         ctypes.byref(opts) if opts is not None else None, ctypes.byref(st) if want_stats else None)
+    return rc, st.as_dict()
+
+
+def batch(imgs, lams, *, rule="max", kernel="auto", tile=None, halo=0, start_phase=0, max_phases=-1, stream=None,
+          stats=True, check=True, debug=0):
+    """Lambda-thin a list of CUDA tensors (each H x W, uint8/uint16) in place, in one device-driven run."""
+    n = len(imgs)
+    if len(lams) != n:
+        raise ValueError("one lambda per image")
+    jobs = (Job * max(n, 1))()
+    for k, (t, lam) in enumerate(zip(imgs, lams)):
+        if not t.is_cuda or t.dim() != 2 or (t.numel() and t.stride(1) != 1):
+            raise ValueError("image %d must be a 2-D CUDA tensor with unit column stride" % k)
+        h, w = t.shape
+        es = t.element_size()
+        jobs[k].img_dev = t.data_ptr() if t.numel() else None
+        jobs[k].w, jobs[k].h = w, h
+        jobs[k].pitch = t.stride(0) * es if h > 1 else w * es
+        jobs[k].dtype = _dtype_code(t)
+        jobs[k].lam = int(lam)
+    sts = (Stats * max(n, 1))()
+    o = options(rule, kernel, tile, halo, start_phase, max_phases, debug)
+    rc = load().thin_batch(jobs, n, ADJ_8_4, _stream_ptr(stream), ctypes.byref(o), sts if stats else None)
+    if check and rc not in (THIN_OK, THIN_ERR_NOT_CONVERGED):
+        raise ThinError(rc, "thin_batch")
+    if stats:
+        return [sts[k].as_dict() for k in range(n)], rc
+    return None, rc

@@ -1,0 +1,100 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/thin.h declares, rejects bad arguments on the host, and its point
+table matches the oracle on all 256 masks.  No compute call reaches a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_1603_09180_gb300 import build as thin_build
+from paper_1603_09180_gb300 import thin
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    thin_build.build()
+    return thin.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "thin.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(thin_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert set(names) >= {"thin_run", "thin_batch", "thin_point_table", "thin_serve_create",
+                          "thin_serve_submit", "thin_serve_poll", "thin_serve_destroy"}
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(thin.EXPORTS) <= set(names)
+    assert "sm_103a" in thin.version()
+
+
+def test_point_table_matches_oracle():
+    tab = thin.point_table()
+    for m in range(256):
+        e = tab[m]
+        tp, tm, lab = oracle.mask_numbers(m)
+        assert (e & 7, (e >> 3) & 7) == (tp, tm), m
+        assert bool(e >> 30 & 1) == (tp == 1 and tm == 1)
+        assert bool(e >> 31 & 1) == (tm >= 2)
+        got = [((e >> (6 + 3 * i)) & 7) - 1 for i in range(8)]
+        # same partition (component numbering may differ)
+        pairs_g = {(i, j) for i in range(8) for j in range(8) if got[i] >= 0 and got[i] == got[j]}
+        pairs_o = {(i, j) for i in range(8) for j in range(8) if lab[i] >= 0 and lab[i] == lab[j]}
+        assert pairs_g == pairs_o, m
+        assert [g >= 0 for g in got] == [l >= 0 for l in lab]
+
+
+def test_host_side_argument_errors(lib):
+    o = thin.options()
+    st = thin.Stats()
+    run = lambda *a: lib.thin_run(*a, ctypes.byref(o), ctypes.byref(st))
+    assert run(None, 10, 10, 10, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
+    assert run(ctypes.c_void_p(4096), -1, 10, 10, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
+    assert run(ctypes.c_void_p(4096), 10, 10, 9, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
+    assert run(ctypes.c_void_p(4096), 10, 10, 20, 7, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
+    assert run(ctypes.c_void_p(4097), 10, 10, 20, thin.U16, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
+    assert run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, thin.ADJ_4_8, None) == thin.THIN_ERR_UNSUPPORTED
+    assert run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, 9, None) == thin.THIN_ERR_ARG
+    # empty and interior-free images are valid no-ops that touch no memory
+    assert run(None, 0, 0, 0, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_OK
+    assert st.converged == 1 and st.phases == 0
+    assert run(ctypes.c_void_p(4096), 2, 50, 2, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_OK
+    bad = thin.options(rule=5)
+    assert lib.thin_run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(bad),
+                        None) == thin.THIN_ERR_ARG
+    bad = thin.options(start_phase=-1)
+    assert lib.thin_run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(bad),
+                        None) == thin.THIN_ERR_ARG
+    assert lib.thin_batch(None, 3, thin.ADJ_8_4, None, None, None) == thin.THIN_ERR_ARG
+    assert lib.thin_batch(None, 0, thin.ADJ_8_4, None, None, None) == thin.THIN_OK
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The library and its binding never load the oracle; no CPU fallback."""
+    pkg = os.path.join(ROOT, "paper_1603_09180_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "liboracle" not in txt, f
+                assert "thin_oracle" not in txt, f
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import importlib
+    mod = importlib.import_module("paper_1603_09180_gb300.thin")
+    with pytest.raises(RuntimeError):
+        saved = mod._lib
+        try:
+            mod._lib = None
+            mod.load(str(tmp_path / "nope.so"))
+        finally:
+            mod._lib = saved

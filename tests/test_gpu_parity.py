@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Integer work, so the bar is bit-exact images, plus equal lowering counts and
+equal last changing phase.  Inputs come from the seeded generator."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_09180_gb300 import synth, thin
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def to_dev(a):
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16).copy()).cuda().view(torch.uint16)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def to_host(t):
+    if t.dtype == torch.uint16:
+        return t.view(torch.int16).cpu().numpy().view(np.uint16)
+    return t.cpu().numpy()
+
+
+def check(img, lam, rule="max", **kw):
+    t = to_dev(img)
+    st = thin.run(t, lam, rule=rule, **kw)
+    torch.cuda.synchronize()
+    ref, rst = oracle.thin(img, lam, oracle.RULE_MAX if rule == "max" else oracle.RULE_MIN,
+                           start_phase=kw.get("start_phase", 0), max_phases=kw.get("max_phases", -1))
+    got = to_host(t)
+    assert np.array_equal(got, ref), "mismatch at %s" % (np.argwhere(got != ref)[:5].tolist(),)
+    assert st["lowered"] == rst["lowered"]
+    assert st["last_change_phase"] == rst["last_change_phase"]
+    if kw.get("max_phases", -1) < 0:
+        assert st["converged"] == 1 and st["rc"] == 0
+    return st, rst
+
+
+SHAPES = [(3, 3), (3, 40), (40, 3), (5, 7), (17, 33), (64, 64), (65, 129), (100, 231), (128, 200)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("lam", [0, 6])
+def test_naive_matches_oracle(shape, lam):
+    img = synth.value_noise_image(*shape, "u8", seed=shape[0] * 7 + shape[1])
+    check(img, lam, kernel="naive")
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("lam", [0, 5, 20])
+def test_tiled_default_matches_oracle(shape, lam):
+    img = synth.value_noise_image(*shape, "u8", seed=shape[0] * 3 + shape[1])
+    check(img, lam)
+
+
+@pytest.mark.parametrize("tile,halo", [((16, 8), 3), ((16, 16), 4), ((32, 16), 8), ((48, 40), 5), ((64, 64), 8),
+                                       ((128, 64), 6), ((224, 32), 7), ((32, 128), 3)])
+@pytest.mark.parametrize("dt", ["u8", "u16"])
+def test_tiled_tile_shapes(tile, halo, dt):
+    img = synth.value_noise_image(150, 170, dt, seed=halo * 11 + tile[0])
+    lam = 7 if dt == "u8" else 100
+    check(img, lam, tile=tile, halo=halo)
+
+
+@pytest.mark.parametrize("rule", ["max", "min"])
+@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+def test_rules(rule, kernel):
+    img = synth.value_noise_image(90, 110, "u8", seed=31)
+    check(img, 12, rule=rule, kernel=kernel)
+
+
+@pytest.mark.parametrize("dt,vmax,lam", [("u16", 4095, 0), ("u16", 4095, 30), ("u16", 65535, 700), ("u8", 255, 255)])
+def test_value_ranges(dt, vmax, lam):
+    img = synth.value_noise_image(96, 120, dt, seed=vmax + lam, vmax=vmax)
+    check(img, lam)
+
+
+def test_white_noise_worst_case():
+    img = synth.uniform_noise_image(130, 150, "u8", seed=4)
+    check(img, 0)
+    check(img, 40)
+
+
+def test_unaligned_pitch_and_offset():
+    """Images whose rows are not 16-byte aligned go through internal buffers."""
+    img = synth.value_noise_image(70, 90, "u8", seed=2)
+    big = np.zeros((80, 101), np.uint8)
+    big[3:73, 5:95] = img
+    t = to_dev(big)
+    view = t[3:73, 5:95]
+    st = thin.run(view, 9)
+    torch.cuda.synchronize()
+    ref, _ = oracle.thin(img, 9)
+    out = to_host(t)
+    assert np.array_equal(out[3:73, 5:95], ref)
+    mask = np.ones_like(big, bool)
+    mask[3:73, 5:95] = False
+    assert np.array_equal(out[mask], big[mask])  # nothing outside the view is touched
+    assert st["converged"] == 1
+
+
+@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+@pytest.mark.parametrize("cap", [1, 4, 7, 13, 40])
+def test_cap_and_resume(kernel, cap):
+    img = synth.value_noise_image(80, 96, "u8", seed=12)
+    full, _ = oracle.thin(img, 10)
+    t = to_dev(img)
+    st = thin.run(t, 10, kernel=kernel, max_phases=cap)
+    torch.cuda.synchronize()
+    part_ref, pst = oracle.thin(img, 10, max_phases=cap)
+    assert np.array_equal(to_host(t), part_ref)
+    if not st["converged"]:
+        assert st["end_phase"] == cap and st["rc"] == thin.THIN_ERR_NOT_CONVERGED
+    st2 = thin.run(t, 10, kernel=kernel, start_phase=cap)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t), full)
+    assert st["lowered"] + st2["lowered"] == oracle.thin(img, 10)[1]["lowered"]
+
+
+def test_start_phase_offsets():
+    img = synth.value_noise_image(60, 75, "u8", seed=8)
+    for g in (1, 2, 3, 6):
+        check(img, 4, start_phase=g)
+
+
+def test_batch_mixed_equals_alone():
+    rng = np.random.default_rng(0)
+    imgs, lams, refs = [], [], []
+    for k in range(14):
+        h, w = int(rng.integers(3, 260)), int(rng.integers(3, 300))
+        dt = "u16" if k % 3 == 0 else "u8"
+        img = synth.value_noise_image(h, w, dt, seed=100 + k)
+        lam = int(rng.choice([0, 10, 25])) * (16 if dt == "u16" else 1)
+        imgs.append(img)
+        lams.append(lam)
+        refs.append(oracle.thin(img, lam))
+    ts = [to_dev(a) for a in imgs]
+    sts, rc = thin.batch(ts, lams)
+    torch.cuda.synchronize()
+    assert rc == 0
+    for t, (ref, rst), st in zip(ts, refs, sts):
+        assert np.array_equal(to_host(t), ref)
+        assert st["lowered"] == rst["lowered"] and st["last_change_phase"] == rst["last_change_phase"]
+
+
+def test_deterministic_repeats():
+    img = synth.value_noise_image(200, 260, "u8", seed=77)
+    outs = []
+    for _ in range(3):
+        t = to_dev(img)
+        thin.run(t, 15)
+        torch.cuda.synchronize()
+        outs.append(to_host(t))
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_config1_full_size():
+    """512 x 512 u8, lambda = 0, seed 1603: bit-exact at full size."""
+    img = synth.value_noise_image(512, 512, "u8", seed=1603)
+    st, rst = check(img, 0)
+    assert st["tiles_visited"] > 0
+
+
+def test_timeout_reports_status_and_context_survives(monkeypatch):
+    """A grid barrier that can never complete (one block does not arrive)
+    gives up after its time limit and reports THIN_ERR_TIMEOUT; the next call
+    on the same context works."""
+    monkeypatch.setenv("THIN_TIMEOUT_NS", "50000000")
+    img = synth.value_noise_image(200, 200, "u8", seed=1)
+    t = to_dev(img)
+    st = thin.run(t, 0, debug=1, check=False)
+    torch.cuda.synchronize()
+    assert st["rc"] == thin.THIN_ERR_TIMEOUT and st["status"] == thin.THIN_ERR_TIMEOUT
+    monkeypatch.delenv("THIN_TIMEOUT_NS")
+    check(img, 0)
