@@ -1,0 +1,363 @@
+"""Benchmark of GB300 lambda-thinning: one JSON line on stdout (rank 0).
+
+Workload (a step): one batch of 64 synthetic 512x512 u8 images, each thinned
+at lambda in {0, 5, 20} (192 jobs), in one thin_batch call -- one persistent
+device-driven launch.  Images are restored from pristine device copies and L2
+is flushed (a 512 MiB write) before every timed step, outside the timed
+region.  Timing: CUDA events on the launching stream around each step,
+barrier + synchronize around the K timed steps, max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain sequential subfield
+schedule) on this host's cores over a bounded sample of the same jobs.
+Multi-GPU: one process per GPU under torchrun; every rank thins its own batch
+(images are independent, no collective on the data path) -> weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "λ-thinned images/s (512² u8) & Gpix-sweeps/s vs HBM roofline; p99 latency"
+N_IMAGES = 64
+LAMBDAS = (0, 5, 20)
+SIDE = 512
+PAPER_IMG_PER_S = 125.0  # Sec. 5.2 / abstract: lambda-skeleton, 512^2 MRI, 2x Xeon E5405 (context only)
+CSRC = os.path.join(ROOT, "paper_1603_09180_gb300", "csrc")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def workload_images():
+    from paper_1603_09180_gb300.synth import value_noise_image
+    return [value_noise_image(SIDE, SIDE, "u8", seed=s) for s in range(N_IMAGES)]
+
+
+def jobs_of(images):
+    return [(k, lam) for k in range(len(images)) for lam in LAMBDAS]
+
+
+# ------------------------------------------------------------------ oracle leg
+
+def _oracle_job(args):
+    img, lam = args
+    import oracle
+    t = time.perf_counter()
+    oracle.thin(img, lam)
+    return time.perf_counter() - t
+
+
+def oracle_sample(images, n_jobs: int, workers: int):
+    """Times the CPU oracle on the first n_jobs jobs (cycling lambda) with a
+    spawn pool of `workers` processes.  Returns (jobs/s, wall seconds)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    todo = [(images[(k // len(LAMBDAS)) % len(images)], LAMBDAS[k % len(LAMBDAS)]) for k in range(n_jobs)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_job, todo, chunksize=1)
+    wall = time.perf_counter() - t0
+    return n_jobs / wall, wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self.path:
+                with open(self.path, "w") as f:
+                    f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def max_over_ranks(vals, world: int, device=None):
+    """Element-wise max of a list of floats over all ranks (identity at world 1)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1603_09180_gb300 import thin
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    thin.load()
+    images = workload_images()
+    jobs = jobs_of(images)
+    n_jobs = len(jobs)
+
+    # CPU baseline (rank 0, N = 1 only) before any device work, in a spawn pool
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        n = max(len(LAMBDAS), (cores // len(LAMBDAS)) * len(LAMBDAS))
+        v, wall = oracle_sample(images, n, min(cores, n))
+        cpu = {"value": v, "unit": "images/s", "cores": min(cores, n), "kind": "oracle",
+               "sample": "%d of the %d jobs (images 0..%d x lambda %s), one process per job, %.1f s wall" % (
+                   n, n_jobs, (n - 1) // len(LAMBDAS), list(LAMBDAS), wall)}
+
+    pristine = torch.from_numpy(np.stack([images[k] for k, _ in jobs])).to(dev)  # (192, 512, 512)
+    work = torch.empty_like(pristine)
+    lams = [lam for _, lam in jobs]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = dict(tile=args.tile, halo=args.halo)
+
+    plan = thin.BatchPlan([work[k] for k in range(n_jobs)], lams, **opts)
+
+    def one_step():
+        plan.run(stream)
+
+    # stats pass: algorithmic units of one step (deterministic)
+    work.copy_(pristine)
+    sts, rc = plan.run(stream, stats=True)
+    assert rc == 0, rc
+    tw = args.tile or 64
+    th = args.tile or 64
+    pix_rounds = sum(s["tiles_visited"] for s in sts) * tw * th * (args.halo or 8) / 4.0
+    alg_bytes = pix_rounds * 2.0  # 1 read + 1 write of a u8 pixel per round over active tiles
+
+    for _ in range(args.warmup):
+        work.copy_(pristine)
+        one_step()
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            work.copy_(pristine)
+            flush.fill_(k & 0xff)  # evict L2 (larger than the 126 MB L2)
+            starts[k].record(stream)
+            one_step()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+
+    # end to end through the C-ABI with host buffers: H2D, thin, D2H every step
+    host_in = torch.from_numpy(np.stack([images[k] for k, _ in jobs])).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2) + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(k & 0xff)
+        e0.record(stream)
+        work.copy_(host_in, non_blocking=True)
+        one_step()
+        host_out.copy_(work, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if k:  # first one is a warm-up
+            e2e_ms.append(e0.elapsed_time(e1))
+    ok = bool(torch.equal(host_out, work.cpu()))
+
+    total_ms, e2e_step_ms = max_over_ranks([total_ms, sum(e2e_ms) / len(e2e_ms)], world, dev)
+    if rank != 0:
+        return None
+
+    ms_per_step = total_ms / args.steps
+    value = world * n_jobs / (total_ms / args.steps / 1e3)
+    achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if not peak:
+        peak, peak_src = 6800.0, "fallback"
+    traffic = None
+    try:
+        tr = json.load(open(TRAFFIC_FILE))
+        if tr.get("source_hash") == kernel_source_hash() and tr.get("workload") == "batch192":
+            traffic = tr.get("traffic_bytes_per_launch")
+    except Exception:
+        pass
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "images/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded value-noise + dark lines; the paper's MRI image is not available)",
+        "config": {"workload": "batch of 64 images 512x512 u8 x lambda {0,5,20} = 192 jobs, one thin_batch launch",
+                   "jobs_per_gpu": n_jobs, "tile": [tw, th], "halo": args.halo or 8,
+                   "l2": "flushed before every timed step (512 MiB write)", "parallelism": "replicas x%d" % world},
+        "gpix_sweeps_per_s": round(world * pix_rounds / (ms_per_step / 1e3) / 1e9, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "traffic": traffic,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "note": "achieved = 2 B x active-tile pixel-rounds / thin_batch device time"},
+        "e2e": {"value": round(world * n_jobs / (e2e_step_ms / 1e3), 2), "unit": "images/s",
+                "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(host_out.numel()),
+                "results_checked": ok},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "paper_context": {"images_per_s": PAPER_IMG_PER_S, "note": "lambda-skeleton on a 512^2 MRI, 8 Xeon cores"},
+        "step_ms": {"min": round(min(step_ms), 4), "p50": round(statistics.median(step_ms), 4),
+                    "max": round(max(step_ms), 4)},
+    }
+    return line
+
+
+def run_reference(args, rank: int, world: int):
+    """The reference arm: the CPU oracle as it stands on this host's cores."""
+    if rank != 0:
+        return None
+    images = workload_images()
+    cores = host_cores()
+    per_step = max(len(LAMBDAS), (cores // len(LAMBDAS)) * len(LAMBDAS))
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(images, len(LAMBDAS), len(LAMBDAS))
+    walls = []
+    for _ in range(args.steps):
+        _, wall = oracle_sample(images, per_step, min(cores, per_step))
+        walls.append(wall)
+    total = sum(walls)
+    value = per_step * args.steps / total
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "impl": "reference",
+        "data": "synthetic (seeded value-noise + dark lines)",
+        "config": {"workload": "batch of 64 images 512x512 u8 x lambda {0,5,20} = 192 jobs; each step a sample "
+                               "of %d jobs on the host cores" % per_step},
+        "cpu_baseline": {"kind": "oracle", "cores": min(cores, per_step), "value": round(value, 3),
+                         "unit": "images/s", "sample": "%d jobs per step, one process per job" % per_step},
+        "e2e": {"value": round(value, 3), "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--halo", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--images", type=int, default=N_IMAGES, help="images per batch (profiling runs use fewer)")
+    args = ap.parse_args(argv)
+    globals()["N_IMAGES"] = args.images
+    if args.warmup < 3 and args.impl == "native":
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        line = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -93,6 +93,26 @@ constexpr PointTable make_point_table()
 
 constexpr PointTable kPointTable = make_point_table();
 
+// For each lower mask m: byte j holds the ring mask of the j-th counted T--
+// component (the 4-components of Gamma^-- that hold a 4-neighbour of x);
+// unused bytes are 0.  Used by the lambda rule of k-divergent points.
+constexpr PointTable make_component_table()
+{
+    PointTable t{};
+    for (unsigned m = 0; m < 256; ++m) {
+        const uint32_t e = point_entry(m);
+        uint32_t v = 0;
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t lab = (e >> (kTabLabelShift + 3 * i)) & 7u;
+            if (lab) v |= (1u << i) << (8 * (lab - 1));
+        }
+        t.v[m] = v;
+    }
+    return t;
+}
+
+constexpr PointTable kComponentTable = make_component_table();
+
 #ifdef __CUDACC__
 
 // Lambda rule for a k-divergent point (Sec. 2.1): at least k-1 of the k

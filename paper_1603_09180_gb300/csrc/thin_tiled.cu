@@ -2,28 +2,36 @@
 //
 // One persistent cooperative launch runs the whole subfield schedule for any
 // number of images.  The schedule advances in steps of H phases (temporal
-// blocking).  In a step every active tile of every image is staged in shared
-// memory with a halo of H pixels by a TMA 2-D tile load, advances H
-// consecutive phases there (the exact region shrinks by one pixel ring per
-// phase, so the TW x TH interior is exact after H phases) and is stored to the
-// other buffer of a ping-pong pair.  A grid barrier separates steps.
+// blocking).  In a step every active tile of every image is visited by one
+// warp: a TMA 2-D tile load stages the tile with a halo of H pixels in the
+// warp's shared memory, the warp advances H consecutive phases there (the exact
+// region shrinks by one pixel ring per phase, so the TW x TH interior is exact
+// after H phases) and stores the interior to the other buffer of a ping-pong
+// pair.  A grid barrier separates steps.
 //
-// Active tiles.  Let a tile step start at global phase g0.  A point can only
-// become lambda-destructible after one of its 8 neighbours changed, so at
-// phase g0 every unstable point lies next to a point that changed during
-// phases g0-3 .. g0-1 (every point was visited in the four phases before its
-// own last visit).  Unstable points spread by at most one pixel per phase, so
-// a tile none of whose 3x3 block of tiles changed in those three phases cannot
-// change during the next H <= min(TW, TH) - 1 phases: it is skipped.  A tile
-// that changed at all in a step is also visited in the next one, which keeps
-// both ping-pong buffers equal on every skipped tile.  The first step (and
-// any step starting within three phases of the first) visits every tile.
-// When a step visits no tile the image is at its fixed point and both buffers
-// hold it.
+// Which points a phase must test.  A point whose 8 neighbours did not change
+// since its own last test (four phases earlier) cannot have become
+// lambda-destructible, so skipping it changes nothing.  Changes are recorded
+// per cell of 8 x 2 pixels as the global index of the last phase that lowered
+// a point in the cell; these stamps persist per image between tile visits.  A
+// group of four points is tested at phase g only if a cell of its 3 x 3 cell
+// neighbourhood changed at a phase >= g - 3.  Stamps start at the first phase
+// of the run, so every point is tested during the first four phases.
+//
+// Which tiles a step visits.  At the start of a step (phase g0) every unstable
+// point lies next to a point that changed during phases g0-3 .. g0-1, and
+// unstable points spread by at most one pixel per phase, so a tile none of
+// whose 3x3 block of tiles changed in those three phases cannot change during
+// the next H <= min(TW, TH) - 1 phases: it is skipped.  A tile that changed at
+// all in a step is also visited in the next one, which keeps both ping-pong
+// buffers equal on every skipped tile.  The first step (and any step starting
+// within three phases of the first) visits every tile.  When a step visits no
+// tile the image is at its fixed point and both buffers hold it.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -36,9 +44,10 @@ namespace thin {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kMaxHalo = 8;
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
 constexpr int kMinHalo = 3;
+constexpr int kNever = -(1 << 30);  // stamp of a cell that never changes
 
 struct ImgDesc {
     CUtensorMap map[2];          // TMA descriptors of buffer 0 and buffer 1
@@ -46,9 +55,11 @@ struct ImgDesc {
     unsigned long long pitch;    // row pitch of both buffers, bytes
     unsigned long long user;     // caller's image
     unsigned long long user_pitch;
+    unsigned long long cells;    // int32 stamps, cells_x x cells_y, relative to the first phase
     int w, h, dtype;
     unsigned lam;
     int tiles_x, tiles_y, tile_base, copy_in;
+    int cells_x, cells_y, pad0, pad1;
 };
 
 struct ImgStat {
@@ -68,6 +79,17 @@ struct Ctl {
     int pad;
 };
 
+// Shared memory of one warp: tile buffer, cell stamps (with a border ring of
+// never-changing cells), work queue and mbarrier.
+struct WarpLayout {
+    int tile_bytes;   // TMA box bytes + 16 (word reads past the last row stay inside)
+    int cell_off;     // offset of the stamps
+    int queue_off;    // offset of the queue (u16 entries)
+    int bar_off;      // offset of the mbarrier
+    int bytes;        // total, 128-aligned
+    int ccols, crows; // stamp grid including the border ring
+};
+
 struct EngineArgs {
     const ImgDesc *imgs;
     ImgStat *st;
@@ -76,15 +98,16 @@ struct EngineArgs {
     Ctl *ctl;
     int n_imgs;
     int total_tiles;
-    int tw, th, halo, rule;
+    int tw, th, halo, hr, rule;  // hr: halo rows in shared memory (halo rounded up to even)
     long long start_phase;
     long long max_phases;
     unsigned long long timeout_ns;
-    int buf_bytes;     // shared bytes reserved per tile buffer
+    WarpLayout wl;
     int debug;         // 1: block 0 never arrives at the first barrier (timeout test)
 };
 
-__device__ const PointTable d_tiled_table = kPointTable;
+__device__ const PointTable d_point_table = kPointTable;
+__device__ const PointTable d_component_table = kComponentTable;
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -167,7 +190,7 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned nblocks, unsigned long long time
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(64);
             }
         }
         __threadfence();
@@ -192,60 +215,309 @@ __device__ __forceinline__ int find_image(const ImgDesc *imgs, int n, int gt)
     return lo;
 }
 
-// H phases of the subfield schedule on a staged tile.  Shared cell (sx, sy)
-// holds image pixel (x0 - A + sx, y0 - H + sy), A = 16 bytes of elements.
-template <typename T>
-__device__ void tile_phases(T *tile, int bw, const ImgDesc &D, int x0, int y0, int tw, int th, int H, int Hs,
-                            long long g0, const uint32_t *tab, int rule, int &nlow, int &chg_j)
+// Exact n / d for n, d < 2^16 with M = floor(2^32 / d) + 1 (M unused when d == 1).
+__device__ __forceinline__ int div_small(int n, int d, uint32_t M)
 {
-    constexpr int A = 16 / int(sizeof(T));
-    for (int j = 0; j < Hs; ++j) {
-        const int p = int((g0 + j) & 3);
-        const int px = p & 1, py = p >> 1;
-        const int r = Hs - 1 - j;
-        const int lox = max(x0 - r, 1), hix = min(x0 + tw + r - 1, D.w - 2);
-        const int loy = max(y0 - r, 1), hiy = min(y0 + th + r - 1, D.h - 2);
-        const int xa = lox + ((px - lox) & 1), ya = loy + ((py - loy) & 1);
-        const int nx = hix >= xa ? (hix - xa) / 2 + 1 : 0;
-        const int ny = hiy >= ya ? (hiy - ya) / 2 + 1 : 0;
-        const int total = nx * ny;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int k = idx / nx, i = idx - k * nx;
-            const int x = xa + 2 * i, y = ya + 2 * k;
-            T *q = tile + (y - y0 + H) * bw + (x - x0 + A);
-            uint32_t nb[8] = {q[1], q[1 - bw], q[-bw], q[-1 - bw], q[-1], q[bw - 1], q[bw], q[bw + 1]};
-            int nl = 0;
-            const uint32_t c2 = lower_point(q[0], nb, tab, D.lam, rule, nl);
-            if (nl) {
-                q[0] = static_cast<T>(c2);
-                if (x >= x0 && x < x0 + tw && y >= y0 && y < y0 + th) {
-                    nlow += nl;
-                    chg_j = j;
-                }
+    return d == 1 ? n : int(__umulhi(uint32_t(n), M));
+}
+
+__device__ __forceinline__ uint32_t div_magic(int d)
+{
+    return d > 1 ? 0xffffffffu / uint32_t(d) + 1u : 0u;
+}
+
+// ------------------------------------------------------------------ SIMD bytes
+
+constexpr uint32_t kMsb8 = 0x80808080u;
+constexpr uint32_t kLsb8 = 0x01010101u;
+
+// Four unsigned byte comparisons a < b at once: bit 7 of each byte of the
+// result is set where byte(a) < byte(b); all other bits are 0.
+// bl = b & 0x7f7f7f7f, bh = b & 0x80808080.  The subtraction of the low
+// seven bits cannot borrow across bytes; bit 7 is then fixed up by hand.
+__device__ __forceinline__ uint32_t lt8(uint32_t a, uint32_t b, uint32_t bl, uint32_t bh)
+{
+    const uint32_t x = a ^ b;
+    const uint32_t r = (a | kMsb8) - bl;
+    const uint32_t dh = (r ^ ~x) & kMsb8;  // bit 7 of the true byte difference a - b
+    return (x & bh) | (~x & dh);           // borrow out of the byte
+}
+
+// 0xff in each byte whose bit 7 is set, else 0x00 (prmt sign replication).
+__device__ __forceinline__ uint32_t msb_to_mask(uint32_t v)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xba98;" : "=r"(r) : "r"(v));
+    return r;
+}
+
+// Rotations of each byte seen as the 8-ring of neighbour bits:
+// rot_prev puts bit i-1 at bit i, rot_next puts bit i+1 at bit i.
+__device__ __forceinline__ uint32_t rot_prev(uint32_t v) { return ((v << 1) & 0xfefefefeu) | ((v >> 7) & kLsb8); }
+__device__ __forceinline__ uint32_t rot_next(uint32_t v) { return ((v >> 1) & 0x7f7f7f7fu) | ((v << 7) & kMsb8); }
+
+// Bit 7 set in every nonzero byte.
+__device__ __forceinline__ uint32_t nonzero8(uint32_t v) { return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) & kMsb8; }
+
+// Merge eight per-direction comparison results (bit 7 per byte) into the
+// ring mask of each point (byte k = mask of point k, bit d = direction d).
+__device__ __forceinline__ uint32_t merge_dirs(const uint32_t lt[8])
+{
+    return (lt[0] >> 7) | (lt[1] >> 6) | (lt[2] >> 5) | (lt[3] >> 4) | (lt[4] >> 3) | (lt[5] >> 2) |
+           (lt[6] >> 1) | lt[7];
+}
+
+// The lowering loop of Sec. 2.2 on four points of one parity at once (bytes
+// of `c`), neighbours fixed (bytes of nb[d], ring order E, NE, N, NW, W, SW,
+// S, SE).  For each point: Gamma^-- is its lower-neighbour mask M; T-- is the
+// number of runs of M once isolated lower corners (those with no lower
+// 4-neighbour beside them, never 4-adjacent to x) are dropped; under (8,4),
+// T+ = T-- except when no 4-neighbour is lower (T-- = 0) or all eight are
+// (T+ = 0), so "destructible" is "exactly one run start".  k-divergent points
+// (two or more runs) are lambda-destructible when at most one of their
+// counted components fails F(x) - F^-(c) <= lambda.  `vm` has 0x01 in the
+// bytes of points that may move.  Returns the bytes lowered (0x01 each) over
+// all iterations; `c` receives the new values, `nin` the lowering steps of the
+// points also in `in`.
+__device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
+                                           const uint32_t *comp, uint32_t lam, int rule, int &nin)
+{
+    uint32_t okacc = 0;
+#pragma unroll 1
+    for (int it = 0; it < 9; ++it) {
+        const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
+        uint32_t lt[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) lt[d] = lt8(nb[d], c, bl, bh);
+        const uint32_t M = merge_dirs(lt);
+        const uint32_t iso = M & 0xaaaaaaaau & ~rot_prev(M) & ~rot_next(M);
+        const uint32_t mc = M ^ iso;                              // counted lower neighbours
+        const uint32_t st = mc & ~rot_prev(mc);                   // starts of their runs
+        const uint32_t t = st & ((st | kMsb8) - kLsb8);           // starts minus the lowest one
+        const uint32_t nzt = nonzero8(t);
+        uint32_t ok = ((nonzero8(st) & ~nzt) >> 7) & vm;          // destructible
+        const uint32_t dv = (nzt >> 7) & vm;                      // k-divergent
+        if (lam != 0 && dv) {
+            // deep lower neighbours: value < F(x) - lambda (none when F(x) <= lambda)
+            const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
+            const uint32_t cl = __vsubus4(c, lrep);
+            const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
+            uint32_t dp[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
+            const uint32_t deep = merge_dirs(dp) & mc;
+            uint32_t todo = dv;
+            while (todo) {
+                const int sh = __ffs(todo) - 1;  // 8 k
+                todo &= todo - 1;
+                const uint32_t e = comp[(M >> sh) & 0xffu];  // component masks, one per byte
+                uint32_t bad;
+                if (rule == 0)  // F^- = max: a component fails when every member is deep
+                    bad = __popc(nonzero8(e)) - __popc(nonzero8(e & ((((mc & ~deep) >> sh) & 0xffu) * kLsb8)));
+                else            // F^- = min: a component fails when some member is deep
+                    bad = __popc(nonzero8(e & (((deep >> sh) & 0xffu) * kLsb8)));
+                if (bad <= 1) ok |= 1u << sh;
             }
         }
-        __syncthreads();
+        if (!ok) break;
+        uint32_t alpha = 0;  // alpha^-: largest lower neighbour
+#pragma unroll
+        for (int d = 0; d < 8; ++d) alpha = __vmaxu4(alpha, nb[d] & msb_to_mask(lt[d]));
+        const uint32_t okm = ok * 0xffu;
+        c = (alpha & okm) | (c & ~okm);
+        okacc |= ok;
+        nin += __popc(ok & in);
+    }
+    return okacc;
+}
+
+// One u8 work item: points (sb + px + 2k, sr), k = 0..3, of one parity in the
+// 8-byte aligned block sb of shared row sr.
+__device__ __forceinline__ uint32_t item_u8(uint8_t *tile, int bw, int sr, int sb, int px, uint32_t vm, uint32_t in,
+                                            const uint32_t *comp, uint32_t lam, int rule, int &nin)
+{
+    const uint8_t *ra = tile + (sr - 1) * bw + sb;  // row y - 1
+    const uint8_t *rb = ra + bw;                     // row y
+    const uint8_t *rc = rb + bw;                     // row y + 1
+    const uint2 wa = *reinterpret_cast<const uint2 *>(ra);
+    const uint2 wb = *reinterpret_cast<const uint2 *>(rb);
+    const uint2 wc = *reinterpret_cast<const uint2 *>(rc);
+    const uint32_t Ea = __byte_perm(wa.x, wa.y, 0x6420), Oa = __byte_perm(wa.x, wa.y, 0x7531);
+    const uint32_t Eb = __byte_perm(wb.x, wb.y, 0x6420), Ob = __byte_perm(wb.x, wb.y, 0x7531);
+    const uint32_t Ec = __byte_perm(wc.x, wc.y, 0x6420), Oc = __byte_perm(wc.x, wc.y, 0x7531);
+    uint32_t nb[8], c;
+    if (px == 0) {
+        const uint32_t La = *reinterpret_cast<const uint32_t *>(ra - 4);
+        const uint32_t Lb = *reinterpret_cast<const uint32_t *>(rb - 4);
+        const uint32_t Lc = *reinterpret_cast<const uint32_t *>(rc - 4);
+        c = Eb;
+        nb[0] = Ob;
+        nb[1] = Oa;
+        nb[2] = Ea;
+        nb[3] = __byte_perm(La, Oa, 0x6543);
+        nb[4] = __byte_perm(Lb, Ob, 0x6543);
+        nb[5] = __byte_perm(Lc, Oc, 0x6543);
+        nb[6] = Ec;
+        nb[7] = Oc;
+    } else {
+        const uint32_t Ra = *reinterpret_cast<const uint32_t *>(ra + 8);
+        const uint32_t Rb = *reinterpret_cast<const uint32_t *>(rb + 8);
+        const uint32_t Rc = *reinterpret_cast<const uint32_t *>(rc + 8);
+        c = Ob;
+        nb[0] = __byte_perm(Eb, Rb, 0x4321);
+        nb[1] = __byte_perm(Ea, Ra, 0x4321);
+        nb[2] = Oa;
+        nb[3] = Ea;
+        nb[4] = Eb;
+        nb[5] = Ec;
+        nb[6] = Oc;
+        nb[7] = __byte_perm(Ec, Rc, 0x4321);
+    }
+    const uint32_t moved = lower4(c, nb, vm, in, comp, lam, rule, nin);
+    if (moved) {
+        uint2 out;
+        if (px == 0)
+            out = make_uint2(__byte_perm(c, Ob, 0x5140), __byte_perm(c, Ob, 0x7362));
+        else
+            out = make_uint2(__byte_perm(Eb, c, 0x5140), __byte_perm(Eb, c, 0x7362));
+        *reinterpret_cast<uint2 *>(tile + sr * bw + sb) = out;
+    }
+    return moved;
+}
+
+// One u16 work item: the same four points, one at a time through the table.
+__device__ __forceinline__ uint32_t item_u16(uint16_t *tile, int bw, int sr, int sb, int px, uint32_t vm, uint32_t in,
+                                             const uint32_t *tab, uint32_t lam, int rule, int &nin)
+{
+    uint32_t moved = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        if (!((vm >> (8 * k)) & 1u)) continue;
+        uint16_t *q = tile + sr * bw + sb + px + 2 * k;
+        uint32_t nb[8] = {q[1], q[1 - bw], q[-bw], q[-1 - bw], q[-1], q[bw - 1], q[bw], q[bw + 1]};
+        int nl = 0;
+        const uint32_t c2 = lower_point(q[0], nb, tab, lam, rule, nl);
+        if (nl) {
+            q[0] = static_cast<uint16_t>(c2);
+            moved |= 1u << (8 * k);
+            if ((in >> (8 * k)) & 1u) nin += nl;
+        }
+    }
+    return moved;
+}
+
+// Per-visit constants, held in registers.
+struct Visit {
+    int w, h;           // image size
+    uint32_t lam;
+    int rule;
+    int x0, y0;         // tile origin in the image
+    int tw, th;         // tile size
+    int H, Hs, hr;      // halo, phases to run, halo rows in shared memory
+    int pad;            // elements of left pad in shared memory (16 B)
+    long long g0;       // global index of the first phase of the step
+    long long start;    // global index of the first phase of the run
+};
+
+// Hs phases of the subfield schedule on a staged tile, visited by one warp.
+// Shared cell (sx, sy) holds image pixel (x0 - pad + sx, y0 - hr + sy); stamp
+// cell (cx, cy) of the grid covers shared columns 8 (cx - 1) .. + 7 and rows
+// 2 (cy - 1) .. + 1 (one border ring of never-changing cells).  Phase j updates
+// the points of its parity within distance Hs-1-j of the tile and off the
+// image border; after Hs phases the tile interior is exact.
+template <typename T>
+__device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_t *queue, const Visit &V,
+                             const uint32_t *tabs, int &nlow, int &chg_j)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_lanes = (1u << lane) - 1u;
+    for (int j = 0; j < V.Hs; ++j) {
+        const long long g = V.g0 + j;
+        const int rel = int(g - V.start);
+        const int p = int(g & 3);
+        const int px = p & 1, py = p >> 1;
+        const int r = V.Hs - 1 - j;
+        const int lox = max(V.x0 - r, 1), hix = min(V.x0 + V.tw + r - 1, V.w - 2);
+        const int loy = max(V.y0 - r, 1), hiy = min(V.y0 + V.th + r - 1, V.h - 2);
+        const int ya = loy + ((py - loy) & 1);
+        const int nrows = hiy >= ya ? (hiy - ya) / 2 + 1 : 0;
+        const int slo = lox - V.x0 + V.pad, shi = hix - V.x0 + V.pad;
+        const int qlo = slo >> 3;
+        const int nq = shi >= slo ? (shi >> 3) - qlo + 1 : 0;
+        const uint32_t Mq = div_magic(nq);
+        const int sra = ya - V.y0 + V.hr;
+        const int items = nrows * nq;
+        // 1. the items whose 3x3 stamp cells changed in the last three phases
+        int qn = 0;
+        for (int base = 0; base < items; base += 32) {
+            const int it = base + lane;
+            bool dirty = false;
+            int code = 0;
+            if (it < items) {
+                const int rk = div_small(it, nq, Mq);
+                const int q = qlo + it - rk * nq;
+                const int sr = sra + 2 * rk;
+                const int32_t *cp = cells + ((sr >> 1) + 1) * ccols + q + 1;
+                int m = max(max(cp[-ccols - 1], cp[-ccols]), cp[-ccols + 1]);
+                m = max(m, max(max(cp[-1], cp[0]), cp[1]));
+                m = max(m, max(max(cp[ccols - 1], cp[ccols]), cp[ccols + 1]));
+                dirty = m >= rel - 3;
+                code = (sr << 6) | q;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, dirty);
+            if (dirty) queue[qn + __popc(bal & lt_lanes)] = uint16_t(code);
+            qn += __popc(bal);
+        }
+        __syncwarp();
+        // 2. test and lower them
+        bool chg = false;
+        for (int k = lane; k < qn; k += 32) {
+            const int code = queue[k];
+            const int sr = code >> 6, q = code & 63, sb = 8 * q;
+            uint32_t vm = 0;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                vm |= (unsigned(sb + px + 2 * kk - slo) <= unsigned(shi - slo) ? 1u : 0u) << (8 * kk);
+            const bool inside = unsigned(sr - V.hr) < unsigned(V.th) && sb >= V.pad && sb < V.pad + V.tw;
+            const uint32_t in = inside ? vm : 0u;
+            uint32_t moved;
+            if (sizeof(T) == 1)
+                moved = item_u8(reinterpret_cast<uint8_t *>(tile), bw, sr, sb, px, vm, in, tabs + 256, V.lam,
+                                V.rule, nlow);
+            else
+                moved = item_u16(reinterpret_cast<uint16_t *>(tile), bw, sr, sb, px, vm, in, tabs, V.lam, V.rule,
+                                 nlow);
+            if (moved) {
+                cells[((sr >> 1) + 1) * ccols + q + 1] = rel;
+                if (moved & in) chg = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, chg)) chg_j = j;
+        __syncwarp();
     }
 }
 
-// Store the tile interior (clipped to the image) to `dst`.
-template <typename T>
-__device__ void tile_store(const T *tile, int bw, const ImgDesc &D, char *dst, int x0, int y0, int tw, int th, int H)
+// Store the tile interior (clipped to the image) to `dst`; 16 bytes of left pad.
+__device__ void tile_store(const uint8_t *tile, int bw_bytes, int es, const Visit &V, char *dst, size_t pitch)
 {
-    constexpr int A = 16 / int(sizeof(T));
-    const int cw = min(tw, D.w - x0), ch = min(th, D.h - y0);
-    if (cw == tw) {
-        const int vpr = tw * int(sizeof(T)) / 16;
-        for (int v = threadIdx.x; v < ch * vpr; v += blockDim.x) {
-            const int row = v / vpr, col = v - row * vpr;
-            const uint4 val = *reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const char *>(tile + (H + row) * bw + A) + col * 16);
-            *reinterpret_cast<uint4 *>(dst + size_t(y0 + row) * D.pitch + size_t(x0) * sizeof(T) + col * 16) = val;
+    const int lane = threadIdx.x & 31;
+    const int cw = min(V.tw, V.w - V.x0) * es, ch = min(V.th, V.h - V.y0);
+    const int rowb = V.tw * es;
+    char *base = dst + size_t(V.y0) * pitch + size_t(V.x0) * es;
+    const uint8_t *src = tile + V.hr * bw_bytes + 16;
+    if (cw == rowb) {
+        const int vpr = rowb / 16;
+        const uint32_t Mv = div_magic(vpr);
+        for (int v = lane; v < ch * vpr; v += 32) {
+            const int row = div_small(v, vpr, Mv), col = v - row * vpr;
+            *reinterpret_cast<uint4 *>(base + size_t(row) * pitch + col * 16) =
+                *reinterpret_cast<const uint4 *>(src + row * bw_bytes + col * 16);
         }
     } else {
-        for (int e = threadIdx.x; e < ch * cw; e += blockDim.x) {
-            const int row = e / cw, col = e - row * cw;
-            reinterpret_cast<T *>(dst + size_t(y0 + row) * D.pitch)[x0 + col] = tile[(H + row) * bw + A + col];
+        const uint32_t Mc = div_magic(cw);
+        for (int e = lane; e < ch * cw; e += 32) {
+            const int row = div_small(e, cw, Mc), col = e - row * cw;
+            base[size_t(row) * pitch + col] = char(src[row * bw_bytes + col]);
         }
     }
 }
@@ -261,37 +533,41 @@ __device__ __forceinline__ void decode(const EngineArgs &P, bool full, const uns
     tx = local - ty * D.tiles_x;
 }
 
-__device__ __forceinline__ void issue(const EngineArgs &P, int img, int tx, int ty, int src, uint8_t *buf,
-                                      uint32_t bar)
-{
-    const ImgDesc &D = P.imgs[img];
-    const int A = D.dtype == THIN_U16 ? 8 : 16;
-    const int es = D.dtype == THIN_U16 ? 2 : 1;
-    const uint32_t bytes = uint32_t((P.tw + 2 * A) * es * (P.th + 2 * P.halo));
-    tma_load_2d(smem_u32(buf), &D.map[src], tx * P.tw - A, ty * P.th - P.halo, bar, bytes);
-}
+constexpr int kSmemTabs = 2048;  // point table (256 x u32) + component table (256 x u32)
 
-__global__ void __launch_bounds__(kThreads) k_engine(EngineArgs P)
+__global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // TMA destinations want 128-byte aligned shared addresses
     uint8_t *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + 1024);
-    uint8_t *bufs[2] = {smem + 1152, smem + 1152 + P.buf_bytes};
-    __shared__ int s_flag, s_nlow, s_maxj;
+    uint32_t *tabs = reinterpret_cast<uint32_t *>(smem);
+    __shared__ int s_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpLayout WL = P.wl;
+    uint8_t *wbase = smem + kSmemTabs + warp * WL.bytes;
+    uint8_t *tile = wbase;
+    int32_t *cells = reinterpret_cast<int32_t *>(wbase + WL.cell_off);
+    uint16_t *queue = reinterpret_cast<uint16_t *>(wbase + WL.queue_off);
+    const uint32_t bar = smem_u32(wbase + WL.bar_off);
 
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = d_tiled_table.v[i];
-    if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        tabs[i] = d_point_table.v[i];
+        tabs[256 + i] = d_component_table.v[i];
+    }
+    if (lane == 0) {
+        mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    uint32_t ph[2] = {0, 0};
+    uint32_t parity = 0;
     long long g0 = P.start_phase;
-    const int H = P.halo;
+    const int H = P.halo, HR = P.hr;
+    const unsigned nwarps = gridDim.x * kWarps;
+    // consecutive items go to different blocks first, so that a step with few
+    // tiles spreads them over the SMs instead of stacking them on one
+    const unsigned gw = warp * gridDim.x + blockIdx.x;
+    const uint32_t Mcc = div_magic(WL.ccols);
     for (int s = 0;; ++s) {
         const long long done = g0 - P.start_phase;
         const int Hs = (P.max_phases >= 0 && P.max_phases - done < H) ? int(P.max_phases - done) : H;
@@ -302,69 +578,95 @@ __global__ void __launch_bounds__(kThreads) k_engine(EngineArgs P)
         unsigned *Lnext = P.lists + size_t((s + 1) % 3) * P.total_tiles;
         if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->list_count[(s + 2) % 3] = 0;
         const int src = s & 1;
-
-        int b = 0;
-        unsigned i = blockIdx.x;
-        int img = 0, tx = 0, ty = 0;
-        if (i < count) {
-            decode(P, full, L, i, img, tx, ty);
-            if (threadIdx.x == 0) issue(P, img, tx, ty, src, bufs[b], smem_u32(&bars[b]));
-        }
         bool failed = false;
-        while (i < count) {
-            const unsigned nxt = i + gridDim.x;
-            int nimg = 0, ntx = 0, nty = 0;
-            if (nxt < count) {
-                decode(P, full, L, nxt, nimg, ntx, nty);
-                if (threadIdx.x == 0) issue(P, nimg, ntx, nty, src, bufs[b ^ 1], smem_u32(&bars[b ^ 1]));
-            }
+        for (unsigned i = gw; i < count; i += nwarps) {
+            int img, tx, ty;
+            decode(P, full, L, i, img, tx, ty);
             const ImgDesc &D = P.imgs[img];
-            const bool ok = mbar_wait(smem_u32(&bars[b]), ph[b], P.timeout_ns);
-            ph[b] ^= 1u;
-            if (!__syncthreads_and(ok)) {
-                if (threadIdx.x == 0) atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
+            Visit V;
+            V.w = D.w;
+            V.h = D.h;
+            V.lam = D.lam;
+            V.rule = P.rule;
+            V.tw = P.tw;
+            V.th = P.th;
+            V.H = H;
+            V.Hs = Hs;
+            V.hr = HR;
+            V.g0 = g0;
+            V.start = P.start_phase;
+            V.x0 = tx * P.tw;
+            V.y0 = ty * P.th;
+            const int u16 = D.dtype == THIN_U16;
+            const int es = u16 ? 2 : 1;
+            V.pad = 16 / es;
+            const int bw = P.tw + 2 * V.pad;  // elements per shared row
+            const size_t pitch = D.pitch;
+            char *dst = reinterpret_cast<char *>(D.buf[src ^ 1]);
+            if (lane == 0) {
+                const uint32_t bytes = uint32_t(bw * es * (P.th + 2 * HR));
+                tma_load_2d(smem_u32(tile), &D.map[src], V.x0 - V.pad, V.y0 - HR, bar, bytes);
+            }
+            // stamps of the region (overlaps the load); the border ring never changes
+            {
+                const int32_t *gc = reinterpret_cast<const int32_t *>(D.cells);
+                const int cx0 = (V.x0 - V.pad) / 8 - 1, cy0 = (V.y0 - HR) / 2 - 1;
+                const int n = WL.ccols * WL.crows;
+#pragma unroll 4
+                for (int e = lane; e < n; e += 32) {
+                    const int cy = div_small(e, WL.ccols, Mcc), cx = e - cy * WL.ccols;
+                    const int gx = cx0 + cx, gy = cy0 + cy;
+                    const bool ring = cx == 0 || cy == 0 || cx == WL.ccols - 1 || cy == WL.crows - 1;
+                    cells[e] = (!ring && gx >= 0 && gy >= 0 && gx < D.cells_x && gy < D.cells_y)
+                                   ? __ldcg(gc + size_t(gy) * D.cells_x + gx)
+                                   : kNever;
+                }
+            }
+            const bool ok = mbar_wait(bar, parity, P.timeout_ns);
+            parity ^= 1u;
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
+                    mbar_wait(bar, parity ^ 1u, P.timeout_ns);  // let the load in flight land (bounded)
+                }
                 failed = true;
                 break;
             }
-            if (threadIdx.x == 0) {
-                s_nlow = 0;
-                s_maxj = -1;
-            }
-            __syncthreads();
+            __syncwarp();
             int nlow = 0, chg_j = -1;
-            const int x0 = tx * P.tw, y0 = ty * P.th;
-            char *dst = reinterpret_cast<char *>(D.buf[src ^ 1]);
-            if (D.dtype == THIN_U16) {
-                const int bw = P.tw + 16;
-                uint16_t *t16 = reinterpret_cast<uint16_t *>(bufs[b]);
-                tile_phases<uint16_t>(t16, bw, D, x0, y0, P.tw, P.th, H, Hs, g0, tab, P.rule, nlow, chg_j);
-                tile_store<uint16_t>(t16, bw, D, dst, x0, y0, P.tw, P.th, H);
-            } else {
-                const int bw = P.tw + 32;
-                uint8_t *t8 = bufs[b];
-                tile_phases<uint8_t>(t8, bw, D, x0, y0, P.tw, P.th, H, Hs, g0, tab, P.rule, nlow, chg_j);
-                tile_store<uint8_t>(t8, bw, D, dst, x0, y0, P.tw, P.th, H);
+            if (u16)
+                visit_phases<uint16_t>(reinterpret_cast<uint16_t *>(tile), bw, cells, WL.ccols, queue, V, tabs, nlow,
+                                       chg_j);
+            else
+                visit_phases<uint8_t>(tile, bw, cells, WL.ccols, queue, V, tabs, nlow, chg_j);
+            tile_store(tile, bw * es, es, V, dst, pitch);
+            // stamps of the interior cells back to the image's stamp grid
+            {
+                int32_t *gc = reinterpret_cast<int32_t *>(D.cells);
+                const int icx = V.tw / 8, icy = V.th / 2;
+                const int cxa = V.x0 / 8, cya = V.y0 / 2;
+                const int ox = V.pad / 8 + 1, oy = HR / 2 + 1;
+                const uint32_t Mi = div_magic(icx);
+#pragma unroll 4
+                for (int e = lane; e < icx * icy; e += 32) {
+                    const int cy = div_small(e, icx, Mi), cx = e - cy * icx;
+                    const int gx = cxa + cx, gy = cya + cy;
+                    if (gx < D.cells_x && gy < D.cells_y)
+                        __stcg(gc + size_t(gy) * D.cells_x + gx, cells[(oy + cy) * WL.ccols + ox + cx]);
+                }
             }
-            // block reduction of the tile's lowering count and last changing phase
-            for (int o = 16; o; o >>= 1) {
-                nlow += __shfl_down_sync(0xffffffffu, nlow, o);
-                chg_j = max(chg_j, __shfl_down_sync(0xffffffffu, chg_j, o));
-            }
-            if ((threadIdx.x & 31) == 0) {
-                if (nlow) atomicAdd(&s_nlow, nlow);
-                if (chg_j >= 0) atomicMax(&s_maxj, chg_j);
-            }
-            // order this tile's generic shared and global writes before later TMA traffic
+            nlow = __reduce_add_sync(0xffffffffu, nlow);
+            const int maxj = __reduce_max_sync(0xffffffffu, chg_j);
+            // order this warp's generic shared and global writes before later TMA traffic
             asm volatile("fence.proxy.async;" ::: "memory");
-            __syncthreads();
-            const int maxj = s_maxj;
-            if (threadIdx.x < 9 && maxj >= 0) {
-                const int dx = int(threadIdx.x % 3) - 1, dy = int(threadIdx.x / 3) - 1;
+            __syncwarp();
+            if (lane < 9 && maxj >= 0) {
+                const int dx = lane % 3 - 1, dy = lane / 3 - 1;
                 const bool self = dx == 0 && dy == 0;
                 const bool late = maxj >= Hs - 3;
-                const int ntx2 = tx + dx, nty2 = ty + dy;
-                if ((self || late) && ntx2 >= 0 && ntx2 < D.tiles_x && nty2 >= 0 && nty2 < D.tiles_y) {
-                    const int gt = D.tile_base + nty2 * D.tiles_x + ntx2;
+                const int ntx = tx + dx, nty = ty + dy;
+                if ((self || late) && ntx >= 0 && ntx < D.tiles_x && nty >= 0 && nty < D.tiles_y) {
+                    const int gt = D.tile_base + nty * D.tiles_x + ntx;
                     if (atomicMax(&P.listed[gt], s + 1) < s + 1) {
                         const unsigned pos = atomicAdd(&P.ctl->list_count[(s + 1) % 3], 1u);
                         Lnext[pos] = unsigned(gt);
@@ -372,21 +674,16 @@ __global__ void __launch_bounds__(kThreads) k_engine(EngineArgs P)
                     }
                 }
             }
-            if (threadIdx.x == 0) {
-                if (s_nlow) atomicAdd(&P.st[img].lowered, (unsigned long long)s_nlow);
+            if (lane == 0) {
+                if (nlow) atomicAdd(&P.st[img].lowered, (unsigned long long)nlow);
                 if (maxj >= 0) atomicMax(&P.st[img].last_change, g0 + maxj);
                 atomicAdd(&P.st[img].tiles_visited, 1ull);
                 atomicMax(&P.st[img].last_step, s);
             }
-            b ^= 1;
-            i = nxt;
-            img = nimg;
-            tx = ntx;
-            ty = nty;
+            __syncwarp();
         }
-        if (failed) {
-            // let a load still in flight land before leaving (bounded)
-            if (i + gridDim.x < count) mbar_wait(smem_u32(&bars[b ^ 1]), ph[b ^ 1], P.timeout_ns);
+        if (__syncthreads_or(failed)) {
+            if (threadIdx.x == 0) atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
             return;
         }
         const bool skip = P.debug == 1 && blockIdx.x == 0 && s == 0;
@@ -443,13 +740,33 @@ EncodeTiledFn encode_fn()
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Shared-memory layout of one warp for tiles tw x th and halo rows hr.  The
+// tile buffer fits the widest element present; the stamp grid and the queue
+// fit u8 geometry (16 pad elements either side), which is the wider in cells.
+WarpLayout warp_layout(int tw, int th, int hr, bool any16)
+{
+    WarpLayout L;
+    const int bw_bytes = any16 ? (tw + 16) * 2 : tw + 32;
+    const int cols8 = (tw + 32) / 8;  // cells per shared row of a u8 tile (u16: fewer)
+    const int rows = th + 2 * hr;
+    L.tile_bytes = int(align_up(size_t(bw_bytes) * rows + 16, 16));
+    L.ccols = cols8 + 2;
+    L.crows = rows / 2 + 2;
+    L.cell_off = L.tile_bytes;
+    const int max_items = (rows / 2 + 1) * (cols8 + 1);
+    L.queue_off = int(align_up(size_t(L.cell_off) + 4 * size_t(L.ccols) * L.crows, 16));
+    L.bar_off = int(align_up(size_t(L.queue_off) + 2 * size_t(max_items), 16));
+    L.bytes = int(align_up(size_t(L.bar_off) + 16, 128));
+    return L;
+}
+
 }  // namespace
 
 void tiled_defaults(int dtype, int *tw, int *th, int *halo)
 {
-    *tw = dtype == THIN_U16 ? 64 : 64;
-    *th = 64;
-    *halo = 8;
+    *tw = 64;
+    *th = 32;
+    *halo = dtype == THIN_U16 ? 8 : 8;
 }
 
 int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, thin_stats *out)
@@ -465,17 +782,22 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
             }
         return THIN_ERR_NOT_CONVERGED;
     }
+    bool any16 = false;
+    for (int k = 0; k < n; ++k) any16 |= jobs[k].dtype == THIN_U16;
     int tw = opt.tile_w, th = opt.tile_h, H = opt.halo;
     {
         int dw, dh, dH;
-        tiled_defaults(jobs[0].dtype, &dw, &dh, &dH);
+        tiled_defaults(any16 ? THIN_U16 : THIN_U8, &dw, &dh, &dH);
         if (!tw) tw = dw;
         if (!th) th = dh;
         if (!H) H = dH;
     }
-    if (H < kMinHalo || H > kMaxHalo || tw < 16 || tw > 224 || tw % 16 || th < 8 || th + 2 * H > 256 ||
+    const int max_halo = any16 ? 8 : 16;  // the 16-byte left pad holds the halo columns
+    if (H < kMinHalo || H > max_halo || tw < 16 || tw > 224 || tw % 16 || th < 8 || th % 2 ||
         std::min(tw, th) < H + 1)
         return THIN_ERR_ARG;
+    const int HR = H + (H & 1);
+    if (th + 2 * HR > 256) return THIN_ERR_ARG;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return THIN_ERR_CUDA;
 
@@ -485,7 +807,7 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
 
     // ---- layout of one scratch allocation
     std::vector<ImgDesc> descs(n);
-    std::vector<size_t> buf_off(n), cpy_off(n);
+    std::vector<size_t> buf_off(n), cpy_off(n), cell_off(n);
     size_t off = 0;
     const size_t o_desc = off;
     off = align_up(off + sizeof(ImgDesc) * n, 256);
@@ -494,7 +816,6 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
     const size_t o_ctl = off;
     off = align_up(off + sizeof(Ctl), 256);
     int total_tiles = 0;
-    bool any16 = false;
     for (int k = 0; k < n; ++k) {
         const JobSpec &J = jobs[k];
         ImgDesc &D = descs[k];
@@ -506,8 +827,9 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
         D.tiles_x = (J.w + tw - 1) / tw;
         D.tiles_y = (J.h + th - 1) / th;
         D.tile_base = total_tiles;
+        D.cells_x = (J.w + 7) / 8;
+        D.cells_y = (J.h + 1) / 2;
         total_tiles += D.tiles_x * D.tiles_y;
-        any16 |= J.dtype == THIN_U16;
         const size_t es = elem_size(J.dtype);
         const bool aligned = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0);
         D.copy_in = aligned ? 0 : 1;
@@ -522,6 +844,12 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
             off = align_up(off + D.pitch * J.h, 256);
         }
     }
+    const size_t o_cells = off;
+    for (int k = 0; k < n; ++k) {
+        cell_off[k] = off;
+        off = align_up(off + sizeof(int32_t) * size_t(descs[k].cells_x) * descs[k].cells_y, 256);
+    }
+    const size_t cells_bytes = off - o_cells;
     const size_t o_listed = off;
     off = align_up(off + sizeof(int) * total_tiles, 256);
     const size_t o_lists = off;
@@ -544,10 +872,11 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
                                   cudaMemcpyDeviceToDevice, stream);
         D.buf[0] = reinterpret_cast<unsigned long long>(b0);
         D.buf[1] = reinterpret_cast<unsigned long long>(b1);
-        const int A = J.dtype == THIN_U16 ? 8 : 16;
+        D.cells = reinterpret_cast<unsigned long long>(base + cell_off[k]);
+        const int pad = J.dtype == THIN_U16 ? 8 : 16;
         const cuuint64_t gdim[2] = {cuuint64_t(J.w), cuuint64_t(J.h)};
         const cuuint64_t gstr[1] = {cuuint64_t(D.pitch)};
-        const cuuint32_t box[2] = {cuuint32_t(tw + 2 * A), cuuint32_t(th + 2 * H)};
+        const cuuint32_t box[2] = {cuuint32_t(tw + 2 * pad), cuuint32_t(th + 2 * HR)};
         const cuuint32_t est[2] = {1, 1};
         for (int q = 0; q < 2; ++q) {
             void *bp = q ? b1 : b0;
@@ -574,6 +903,7 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_stat, st0.data(), sizeof(ImgStat) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_listed, 0xff, sizeof(int) * total_tiles, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_cells, 0, cells_bytes, stream);  // every cell: changed at the first phase
 
     EngineArgs P;
     std::memset(&P, 0, sizeof P);
@@ -587,21 +917,21 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
     P.tw = tw;
     P.th = th;
     P.halo = H;
+    P.hr = HR;
     P.rule = opt.rule;
     P.start_phase = opt.start_phase;
     P.max_phases = opt.max_phases;
     P.timeout_ns = 2000000000ull;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
     P.debug = opt.reserved;
-    P.buf_bytes = int(align_up(size_t(tw + 32) * (th + 2 * H), 128));  // 32 bytes of pad = 2 x 16 B either side
-    if (any16) P.buf_bytes = int(align_up(size_t(tw + 16) * 2 * (th + 2 * H), 128));
-    const int smem = 128 + 1152 + 2 * P.buf_bytes;
+    P.wl = warp_layout(tw, th, HR, any16);
+    const int smem = 128 + kSmemTabs + kWarps * P.wl.bytes;
 
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, smem);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    int grid = std::max(1, std::min(sms * per_sm, total_tiles));
+    int grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
     if (opt.reserved == 1) grid = std::max(grid, std::min(2, sms * per_sm));
     if (e == cudaSuccess) {
         void *args[] = {&P};

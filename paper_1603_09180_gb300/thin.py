@@ -195,3 +195,37 @@ def batch(imgs, lams, *, rule="max", kernel="auto", tile=None, halo=0, start_pha
     if stats:
         return [sts[k].as_dict() for k in range(n)], rc
     return None, rc
+
+
+class BatchPlan:
+    """A batch whose job records are marshalled once; ``run`` calls thin_batch.
+
+    The tensors must stay alive (and at the same addresses) while the plan is used."""
+
+    def __init__(self, imgs, lams, *, rule="max", kernel="auto", tile=None, halo=0, start_phase=0, max_phases=-1,
+                 debug=0):
+        self.n = len(imgs)
+        if len(lams) != self.n:
+            raise ValueError("one lambda per image")
+        self.jobs = (Job * max(self.n, 1))()
+        for k, (t, lam) in enumerate(zip(imgs, lams)):
+            if not t.is_cuda or t.dim() != 2 or (t.numel() and t.stride(1) != 1):
+                raise ValueError("image %d must be a 2-D CUDA tensor with unit column stride" % k)
+            h, w = t.shape
+            es = t.element_size()
+            self.jobs[k].img_dev = t.data_ptr() if t.numel() else None
+            self.jobs[k].w, self.jobs[k].h = w, h
+            self.jobs[k].pitch = t.stride(0) * es if h > 1 else w * es
+            self.jobs[k].dtype = _dtype_code(t)
+            self.jobs[k].lam = int(lam)
+        self.opts = options(rule, kernel, tile, halo, start_phase, max_phases, debug)
+        self.stats = (Stats * max(self.n, 1))()
+
+    def run(self, stream=None, stats=False, check=True):
+        rc = load().thin_batch(self.jobs, self.n, ADJ_8_4, _stream_ptr(stream), ctypes.byref(self.opts),
+                               self.stats if stats else None)
+        if check and rc not in (THIN_OK, THIN_ERR_NOT_CONVERGED):
+            raise ThinError(rc, "thin_batch")
+        if stats:
+            return [self.stats[k].as_dict() for k in range(self.n)], rc
+        return None, rc
