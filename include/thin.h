@@ -51,6 +51,7 @@ extern "C" {
 #define THIN_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
 #define THIN_ERR_CUDA (-6)          /* a CUDA runtime call failed */
 #define THIN_EAGAIN (-7)            /* serving: over the memory budget and the queue is full */
+#define THIN_ERR_TOO_LARGE (-8)     /* thin_run_noalloc: the image needs more than its fixed scratch */
 
 typedef enum { THIN_U8 = 0, THIN_U16 = 1 } thin_dtype;
 typedef enum { THIN_ADJ_8_4 = 0, THIN_ADJ_4_8 = 1 } thin_adj;
@@ -140,6 +141,36 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
  *   bit 31     k-divergent (T-- >= 2)
  */
 void thin_point_table(uint32_t out[256]);
+
+/*
+ * thin_run_noalloc: thin_run with the tiled engine for callers that cannot
+ * allocate device memory, e.g. an application that hands every byte of device
+ * memory to its own allocator up front, or code that runs while another
+ * thread of the process captures a CUDA graph in global capture mode, where
+ * allocation calls are refused.  The paper has no counterpart: this is a
+ * property of the library, not of the method.
+ *
+ * Arguments, layout, result and stats are those of thin_run (the kernel
+ * option is ignored: the tiled engine always runs).  Scratch memory comes
+ * from one array of THIN_NOALLOC_SCRATCH_BYTES that the library declares in
+ * device memory; every GPU that loads the library holds it until the process
+ * exits.  The call allocates nothing.
+ *   - An image whose scratch (a second image-sized buffer, one more if its
+ *     rows are not 16-byte aligned, 4 bytes per 8 x 2 pixels of change stamps
+ *     and a few words per 64 x 32 tile) does not fit returns
+ *     THIN_ERR_TOO_LARGE and is left untouched.  16 MiB holds, for example,
+ *     a 3500 x 3500 u8 or a 2500 x 2500 u16 image with 16-byte aligned rows
+ *     (unaligned rows need the extra buffer: 2048 x 2048 u8 still fits).
+ *   - The first call on a device looks up the array's device address; make it
+ *     before any stream capture begins.
+ *   - Every call uses the same array and overwrites what the previous call
+ *     left there (the call itself resets everything it reads).  Calls that
+ *     can overlap on the GPU -- on different streams, or from several host
+ *     threads -- race on the array and give wrong results: serialise them.
+ */
+#define THIN_NOALLOC_SCRATCH_BYTES (16u << 20)
+int thin_run_noalloc(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
+                     thin_adj adj, void *stream, const thin_options *opt, thin_stats *out);
 
 /* Library version string. */
 const char *thin_version(void);

@@ -975,3 +975,250 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
 }
 
 }  // namespace thin
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot allocate device memory at the moment they want to thin
+// an image: an application that owns all device memory through its own fixed
+// budget, or code that runs while another thread of the process is capturing
+// a CUDA graph in global capture mode (where allocation calls are refused).
+// thin_run_noalloc serves them with the tiled engine and no allocation at all:
+// its scratch (the second ping-pong buffer, the change stamps, the worklists
+// and the control words) lives in one fixed array in device memory that the
+// library declares at file scope.  Every GPU that loads the library holds the
+// array until the process exits.
+static __device__ __align__(256) unsigned char g_thin_noalloc_scratch[THIN_NOALLOC_SCRATCH_BYTES];
+
+namespace thin {
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[256] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (in host code the array's name is only a host-side stand-in).
+cudaError_t noalloc_scratch(void **base)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_thin_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_base[dev] = p;
+    }
+    *base = g_noalloc_base[dev];
+    return cudaSuccess;
+}
+
+// The tiled engine on one image, with every piece of scratch carved from the
+// fixed array.  Same kernels, launch and result as tiled_run.
+int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    if (opt.max_phases == 0) {
+        if (out) {
+            std::memset(out, 0, sizeof *out);
+            out->status = THIN_ERR_NOT_CONVERGED;
+            out->last_change_phase = -1;
+            out->end_phase = opt.start_phase;
+        }
+        return THIN_ERR_NOT_CONVERGED;
+    }
+    const bool is16 = J.dtype == THIN_U16;
+    int tw = opt.tile_w, th = opt.tile_h, H = opt.halo;
+    {
+        int dw, dh, dH;
+        tiled_defaults(J.dtype, &dw, &dh, &dH);
+        if (!tw) tw = dw;
+        if (!th) th = dh;
+        if (!H) H = dH;
+    }
+    const int max_halo = is16 ? 8 : 16;
+    if (H < kMinHalo || H > max_halo || tw < 16 || tw > 224 || tw % 16 || th < 8 || th % 2 ||
+        std::min(tw, th) < H + 1)
+        return THIN_ERR_ARG;
+    const int HR = H + (H & 1);
+    if (th + 2 * HR > 256) return THIN_ERR_ARG;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return THIN_ERR_CUDA;
+
+    ImgDesc D;
+    std::memset(&D, 0, sizeof D);
+    D.w = J.w;
+    D.h = J.h;
+    D.dtype = J.dtype;
+    D.lam = J.lam;
+    D.tiles_x = (J.w + tw - 1) / tw;
+    D.tiles_y = (J.h + th - 1) / th;
+    D.tile_base = 0;
+    D.cells_x = (J.w + 7) / 8;
+    D.cells_y = (J.h + 1) / 2;
+    const int total_tiles = D.tiles_x * D.tiles_y;
+    const size_t es = elem_size(J.dtype);
+    const bool aligned = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0);
+    D.copy_in = aligned ? 0 : 1;
+    D.pitch = aligned ? J.pitch : align_up(size_t(J.w) * es, 128);
+    D.user = reinterpret_cast<unsigned long long>(J.img);
+    D.user_pitch = J.pitch;
+
+    // layout inside the fixed array (same pieces as tiled_run, one image)
+    size_t off = 0;
+    const size_t o_desc = off;
+    off = align_up(off + sizeof(ImgDesc), 256);
+    const size_t o_stat = off;
+    off = align_up(off + sizeof(ImgStat), 256);
+    const size_t o_ctl = off;
+    off = align_up(off + sizeof(Ctl), 256);
+    const size_t o_buf = off;
+    off = align_up(off + D.pitch * J.h, 256);
+    const size_t o_cpy = off;
+    if (D.copy_in) off = align_up(off + D.pitch * J.h, 256);
+    const size_t o_cells = off;
+    const size_t cells_bytes = sizeof(int32_t) * size_t(D.cells_x) * D.cells_y;
+    off = align_up(off + cells_bytes, 256);
+    const size_t o_listed = off;
+    off = align_up(off + sizeof(int) * total_tiles, 256);
+    const size_t o_lists = off;
+    off = align_up(off + sizeof(unsigned) * 3 * size_t(total_tiles), 256);
+    if (off > THIN_NOALLOC_SCRATCH_BYTES) return THIN_ERR_TOO_LARGE;
+
+    char *base = nullptr;
+    cudaError_t e = noalloc_scratch(reinterpret_cast<void **>(&base));
+    if (e != cudaSuccess) return cuda_status(e);
+
+    void *b0 = D.copy_in ? static_cast<void *>(base + o_cpy) : J.img;
+    void *b1 = base + o_buf;
+    if (D.copy_in)
+        e = cudaMemcpy2DAsync(b0, D.pitch, J.img, J.pitch, size_t(J.w) * es, J.h, cudaMemcpyDeviceToDevice, stream);
+    D.buf[0] = reinterpret_cast<unsigned long long>(b0);
+    D.buf[1] = reinterpret_cast<unsigned long long>(b1);
+    D.cells = reinterpret_cast<unsigned long long>(base + o_cells);
+    {
+        const int pad = is16 ? 8 : 16;
+        const cuuint64_t gdim[2] = {cuuint64_t(J.w), cuuint64_t(J.h)};
+        const cuuint64_t gstr[1] = {cuuint64_t(D.pitch)};
+        const cuuint32_t box[2] = {cuuint32_t(tw + 2 * pad), cuuint32_t(th + 2 * HR)};
+        const cuuint32_t est[2] = {1, 1};
+        for (int q = 0; q < 2; ++q) {
+            CUresult r = enc(&D.map[q], is16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                             q ? b1 : b0, gdim, gstr, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return THIN_ERR_ARG;
+        }
+    }
+    // the array keeps the previous call's contents: set everything the engine reads
+    ImgStat st0;
+    st0.lowered = 0;
+    st0.tiles_visited = 0;
+    st0.last_change = -1;
+    st0.last_step = -1;
+    st0.last_listed = 0;
+    Ctl ctl0;
+    std::memset(&ctl0, 0, sizeof ctl0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_desc, &D, sizeof D, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_stat, &st0, sizeof st0, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_listed, 0xff, sizeof(int) * total_tiles, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_cells, 0, cells_bytes, stream);
+
+    EngineArgs P;
+    std::memset(&P, 0, sizeof P);
+    P.imgs = reinterpret_cast<const ImgDesc *>(base + o_desc);
+    P.st = reinterpret_cast<ImgStat *>(base + o_stat);
+    P.listed = reinterpret_cast<int *>(base + o_listed);
+    P.lists = reinterpret_cast<unsigned *>(base + o_lists);
+    P.ctl = reinterpret_cast<Ctl *>(base + o_ctl);
+    P.n_imgs = 1;
+    P.total_tiles = total_tiles;
+    P.tw = tw;
+    P.th = th;
+    P.halo = H;
+    P.hr = HR;
+    P.rule = opt.rule;
+    P.start_phase = opt.start_phase;
+    P.max_phases = opt.max_phases;
+    P.timeout_ns = 2000000000ull;
+    if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
+    P.debug = 0;
+    P.wl = warp_layout(tw, th, HR, is16);
+    const int smem = 128 + kSmemTabs + kWarps * P.wl.bytes;
+
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
+    if (e == cudaSuccess) {
+        void *args[] = {&P};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_engine), dim3(grid), dim3(kThreads), args, smem,
+                                        stream);
+    }
+    if (e == cudaSuccess) {
+        k_copy_out<<<dim3(64, 1), 256, 0, stream>>>(P.imgs, P.st, 1);
+        e = cudaGetLastError();
+    }
+    int rc = THIN_OK;
+    if (e == cudaSuccess && out) {
+        ImgStat S;
+        Ctl ctl;
+        e = cudaMemcpyAsync(&S, P.st, sizeof S, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess) {
+            std::memset(out, 0, sizeof *out);
+            const long long steps = S.last_step + 1;
+            long long phases = steps * H;
+            if (opt.max_phases >= 0) phases = std::min<long long>(phases, opt.max_phases);
+            out->converged = (S.last_listed <= S.last_step && ctl.error == 0) ? 1 : 0;
+            out->status = ctl.error ? ctl.error : (out->converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
+            out->phases = phases;
+            out->lowered = (int64_t)S.lowered;
+            out->last_change_phase = S.last_change;
+            out->end_phase = opt.start_phase + phases;
+            out->tiles_visited = (int64_t)S.tiles_visited;
+            out->steps = steps;
+            rc = out->status;
+        }
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    return rc;
+}
+
+}  // namespace
+}  // namespace thin
+
+extern "C" int thin_run_noalloc(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
+                                thin_adj adj, void *stream, const thin_options *opt, thin_stats *out)
+{
+    thin_options o;
+    thin_default_options(&o);
+    if (opt) o = *opt;
+    if (adj == THIN_ADJ_4_8) return THIN_ERR_UNSUPPORTED;
+    if (adj != THIN_ADJ_8_4) return THIN_ERR_ARG;
+    if (o.rule != THIN_RULE_MAX && o.rule != THIN_RULE_MIN) return THIN_ERR_ARG;
+    if (o.start_phase < 0 || o.tile_w < 0 || o.tile_h < 0 || o.halo < 0) return THIN_ERR_ARG;
+    if (w < 0 || h < 0 || (dt != THIN_U8 && dt != THIN_U16)) return THIN_ERR_ARG;
+    const size_t es = dt == THIN_U16 ? 2 : 1;
+    if (w > 0 && h > 0) {
+        if (!img_dev || pitch_bytes < size_t(w) * es) return THIN_ERR_ARG;
+        if (es == 2 && ((reinterpret_cast<uintptr_t>(img_dev) & 1) || (pitch_bytes & 1))) return THIN_ERR_ARG;
+    }
+    if (w < 3 || h < 3) {  // empty, or no interior point: nothing to do
+        if (out) {
+            std::memset(out, 0, sizeof *out);
+            out->converged = 1;
+            out->last_change_phase = -1;
+            out->end_phase = o.start_phase;
+        }
+        return THIN_OK;
+    }
+    thin::JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda};
+    return thin::tiled_run_noalloc(j, o, static_cast<cudaStream_t>(stream), out);
+}

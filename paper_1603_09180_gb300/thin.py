@@ -23,9 +23,11 @@ THIN_ERR_NOT_CONVERGED = -4
 THIN_ERR_TIMEOUT = -5
 THIN_ERR_CUDA = -6
 THIN_EAGAIN = -7
+THIN_ERR_TOO_LARGE = -8
 ERRORS = {THIN_ERR_ARG: "bad argument", THIN_ERR_UNSUPPORTED: "unsupported", THIN_ERR_OOM: "out of memory",
           THIN_ERR_NOT_CONVERGED: "not converged", THIN_ERR_TIMEOUT: "device wait timed out",
-          THIN_ERR_CUDA: "CUDA error", THIN_EAGAIN: "over budget, try again"}
+          THIN_ERR_CUDA: "CUDA error", THIN_EAGAIN: "over budget, try again",
+          THIN_ERR_TOO_LARGE: "image too large for the fixed scratch"}
 
 U8, U16 = 0, 1
 ADJ_8_4, ADJ_4_8 = 0, 1
@@ -91,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.thin_serve_poll.restype = i32
     lib.thin_serve_destroy.argtypes = [vp]
     lib.thin_serve_destroy.restype = i32
+    lib.thin_run_noalloc.argtypes = lib.thin_run.argtypes
+    lib.thin_run_noalloc.restype = i32
     _lib = lib
     return lib
 
