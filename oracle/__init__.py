@@ -91,7 +91,9 @@ def _load():
 
 
 def _i32(img) -> np.ndarray:
-    a = np.ascontiguousarray(np.asarray(img), dtype=np.int32)
+    """A fresh C-contiguous int32 copy: the C routines work in place and must
+    never touch the caller's array."""
+    a = np.array(np.asarray(img), dtype=np.int32, order="C", copy=True)
     if a.ndim != 2:
         raise ValueError("image must be 2-D (H, W)")
     return a

@@ -285,3 +285,14 @@ def test_u16_and_tiny_shapes():
         o, st = oracle.thin(a, 0) if a.size else (a, None)
         if a.size and min(shape) < 3:
             assert np.array_equal(o, a)
+
+
+def test_oracle_leaves_inputs_untouched():
+    """The wrapper works on a copy for every input dtype (int32 included)."""
+    for dt in (np.int32, np.uint8, np.uint16):
+        img = (np.arange(64).reshape(8, 8) * 7 % 23).astype(dt)
+        keep = img.copy()
+        oracle.thin(img, 3)
+        oracle.thin_queue(img, 3)
+        oracle.thin_minvalue(img, 3)
+        assert np.array_equal(img, keep)
