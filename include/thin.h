@@ -61,9 +61,17 @@ typedef enum { THIN_ADJ_8_4 = 0, THIN_ADJ_4_8 = 1 } thin_adj;
  * THIN_RULE_MIN the smallest. */
 typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
 
-/* Kernel family: AUTO picks the tiled kernel; NAIVE runs one launch per phase
- * straight from global memory (the reference slice). */
-typedef enum { THIN_KERNEL_AUTO = 0, THIN_KERNEL_NAIVE = 1, THIN_KERNEL_TILED = 2 } thin_kernel;
+/* Kernel family.  RESIDENT holds each image in the shared memory of one
+ * thread-block cluster (images up to about 1.7 MB); TILED streams 64 x 32
+ * tiles through shared memory (any size); AUTO picks RESIDENT for images that
+ * fit and TILED for the rest; NAIVE runs one launch per phase straight from
+ * global memory (the reference slice). */
+typedef enum {
+    THIN_KERNEL_AUTO = 0,
+    THIN_KERNEL_NAIVE = 1,
+    THIN_KERNEL_TILED = 2,
+    THIN_KERNEL_RESIDENT = 3
+} thin_kernel;
 
 typedef struct {
     int32_t rule;        /* thin_rule */

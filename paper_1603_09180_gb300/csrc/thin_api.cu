@@ -1,6 +1,7 @@
 // thin_api.cu -- the C-ABI of libthin.so: argument checks and dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -21,7 +22,7 @@ namespace {
 int check_options(const thin_options &o)
 {
     if (o.rule != THIN_RULE_MAX && o.rule != THIN_RULE_MIN) return THIN_ERR_ARG;
-    if (o.kernel < THIN_KERNEL_AUTO || o.kernel > THIN_KERNEL_TILED) return THIN_ERR_ARG;
+    if (o.kernel < THIN_KERNEL_AUTO || o.kernel > THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;
     if (o.start_phase < 0) return THIN_ERR_ARG;
     if (o.tile_w < 0 || o.tile_h < 0 || o.halo < 0) return THIN_ERR_ARG;
     return THIN_OK;
@@ -39,6 +40,60 @@ int check_image(const void *img, int w, int h, size_t pitch, int dt)
     if (es == 2 && ((reinterpret_cast<uintptr_t>(img) & 1) || (pitch & 1))) return THIN_ERR_ARG;
     if (w < 3 || h < 3) return 1;
     return 0;
+}
+
+// Runs images on the resident engine where they fit (AUTO, RESIDENT) and on
+// the tiled engine otherwise; stats land at the images' own positions.
+int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out)
+{
+    const int n = int(specs.size());
+    std::vector<int> cls(n, 0);
+    if (o.kernel == THIN_KERNEL_AUTO || o.kernel == THIN_KERNEL_RESIDENT) {
+        const size_t limit = resident_smem_limit();
+        for (int k = 0; k < n; ++k)
+            cls[k] = resident_cluster_size(specs[k].w, specs[k].h, specs[k].dtype, limit, nullptr, nullptr);
+    }
+    int eligible = 0, sms = 0, dev = 0;
+    for (int k = 0; k < n; ++k) eligible += cls[k] > 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // few images: spread each over more blocks of a wider cluster
+    int spread = 1;
+    while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms) spread *= 2;
+    int rc = THIN_OK;
+    for (int C = 1; C <= 8; C *= 2) {
+        std::vector<JobSpec> group;
+        std::vector<int> where;
+        for (int k = 0; k < n; ++k)
+            if (cls[k] > 0 && std::max(cls[k], spread) == C) {
+                group.push_back(specs[k]);
+                where.push_back(k);
+            }
+        if (group.empty()) continue;
+        std::vector<thin_stats> st(out ? group.size() : 0);
+        const int r = resident_run(group.data(), int(group.size()), C, o, s, out ? st.data() : nullptr);
+        if (out)
+            for (size_t k = 0; k < group.size(); ++k) out[where[k]] = st[k];
+        if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;
+        if (r != THIN_OK && rc == THIN_OK) rc = r;
+    }
+    std::vector<JobSpec> rest;
+    std::vector<int> where;
+    for (int k = 0; k < n; ++k)
+        if (cls[k] == 0) {
+            rest.push_back(specs[k]);
+            where.push_back(k);
+        }
+    if (!rest.empty()) {
+        if (o.kernel == THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;  // does not fit on chip
+        std::vector<thin_stats> st(out ? rest.size() : 0);
+        const int r = tiled_run(rest.data(), int(rest.size()), o, s, out ? st.data() : nullptr);
+        if (out)
+            for (size_t k = 0; k < rest.size(); ++k) out[where[k]] = st[k];
+        if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;
+        if (r != THIN_OK && rc == THIN_OK) rc = r;
+    }
+    return rc;
 }
 
 void noop_stats(const thin_options &o, thin_stats *s)
@@ -93,7 +148,8 @@ int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uin
     JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (o.kernel == THIN_KERNEL_NAIVE) return naive_run(j, o, s, out);
-    return tiled_run(&j, 1, o, s, out);
+    if (o.kernel == THIN_KERNEL_TILED) return tiled_run(&j, 1, o, s, out);
+    return dispatch(std::vector<JobSpec>{j}, o, s, out);
 }
 
 int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const thin_options *opt, thin_stats *out)
@@ -132,8 +188,10 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
             if (r != THIN_OK && rc == THIN_OK) rc = r;
             if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;
         }
-    } else {
+    } else if (o.kernel == THIN_KERNEL_TILED) {
         rc = tiled_run(specs.data(), int(specs.size()), o, s, out ? st.data() : nullptr);
+    } else {
+        rc = dispatch(specs, o, s, out ? st.data() : nullptr);
     }
     if (out)
         for (size_t k = 0; k < specs.size(); ++k) out[where[k]] = st[k];

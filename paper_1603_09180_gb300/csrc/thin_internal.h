@@ -27,6 +27,13 @@ int naive_run(const JobSpec &job, const thin_options &opt, cudaStream_t stream, 
 // one persistent cooperative launch for any number of images.
 int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, thin_stats *out);
 
+// Resident engine: each image held in the shared memory of one thread-block
+// cluster of C blocks (1, 2, 4 or 8) for its whole run.
+int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cudaStream_t stream, thin_stats *out);
+// Smallest cluster whose shared memory holds a w x h image of `dtype`, 0 if none.
+int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_out, int *rp_out);
+size_t resident_smem_limit();
+
 // Defaults of the tiled engine for a dtype (tile width/height in pixels, halo).
 void tiled_defaults(int dtype, int *tw, int *th, int *halo);
 

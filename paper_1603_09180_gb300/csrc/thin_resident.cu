@@ -1,0 +1,541 @@
+// thin_resident.cu -- the resident lambda-thinning engine: each image lives
+// in the shared memory of one thread-block cluster for its whole run.
+//
+// Block r of a cluster of C blocks holds image rows [r R, r R + R); a point
+// on the first or last of its rows reads the neighbouring row straight from
+// the next block's shared memory (distributed shared memory).  A phase only
+// writes rows of its own parity, and its points read only rows of the other
+// parity, so these reads never race; a cluster barrier ends every phase.
+// Clusters take images from a device-wide counter, so images of different
+// lengths run side by side without any grid-wide synchronisation.
+//
+// Which points a phase tests.  Each block keeps, per cell of 8 x 2 pixels, a
+// bit "lowered a point in phase g" for the last four phases (four rotating
+// bitmaps).  Phase g tests the 4-point group of a cell only if a cell of its
+// 3 x 3 cell neighbourhood changed in phases g-3 .. g-1: a point none of whose
+// neighbours moved since its own last test cannot have become
+// lambda-destructible.  The first four phases of a run test everything.  The
+// run stops once three phases in a row changed nothing (the image is then at
+// the fixed point of the schedule) or at the phase cap.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "thin_common.cuh"
+#include "thin_internal.h"
+#include "thin_simd.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace thin {
+
+namespace {
+
+constexpr int kResThreads = 1024;
+
+struct ResJob {
+    unsigned long long img;    // the caller's image, thinned in place
+    unsigned long long pitch;  // bytes between rows
+    int w, h, dtype;
+    unsigned lam;
+    int rows;   // image rows per block (even)
+    int rp;     // shared row pitch in bytes: 16 B pad | w * es | pad to 16 | 16 B pad
+    int cw;     // cells per row = ceil(w / 8)
+    int wpr;    // bitmap words per cell row = ceil(cw / 32)
+    int bulk;   // rows are 16-byte aligned and a multiple of 16 bytes: stage them by bulk copy
+    int index;  // position of the job in the caller's list
+    int pad0, pad1;
+};
+
+struct ResStat {
+    unsigned long long lowered;
+    long long last_change;  // global phase index, -1 if none
+    long long phases;
+    int converged;
+    int error;
+};
+
+struct ResCtl {
+    unsigned next_job;
+    int error;
+    int pad[2];
+};
+
+struct ResArgs {
+    const ResJob *jobs;
+    ResStat *st;
+    ResCtl *ctl;
+    int njobs;
+    int rule;
+    long long start_phase;
+    long long max_phases;
+    unsigned long long timeout_ns;
+};
+
+__device__ const PointTable d_res_point_table = kPointTable;
+__device__ const PointTable d_res_component_table = kComponentTable;
+
+// Shared-memory map of one block for a job.
+constexpr int kOffTabs = 0;      // point table + component table, 2 KiB
+constexpr int kOffCtrl = 2048;   // control words
+constexpr int kOffBar = 2176;    // mbarrier of the row staging
+constexpr int kOffRows = 2304;   // image rows (16-byte aligned)
+
+struct Ctrl {
+    int job;
+    int qn[2];          // queue length, double-buffered by phase parity
+    int pad;
+    long long last;     // last phase in which this block lowered a point, -1 if none
+    unsigned long long nlow;
+    long long peer_last[8];  // every block's `last`, pushed by the blocks themselves each phase
+};
+
+__host__ __device__ inline size_t res_bits_off(int rows, int rp) { return (kOffRows + size_t(rows) * rp + 15) / 16 * 16; }
+// four change bitmaps, then the OR of the last three with one cell row above and below
+__host__ __device__ inline size_t res_rec_off(int rows, int rp, int wpr)
+{
+    return res_bits_off(rows, rp) + size_t(4) * 4 * (rows / 2) * wpr;
+}
+__host__ __device__ inline size_t res_queue_off(int rows, int rp, int wpr)
+{
+    return res_rec_off(rows, rp, wpr) + size_t(4) * (rows / 2 + 2) * wpr;
+}
+__host__ __device__ inline size_t res_smem_bytes(int rows, int rp, int cw, int wpr)
+{
+    return res_queue_off(rows, rp, wpr) + size_t(2) * (rows / 2) * cw + 16;
+}
+
+__device__ __forceinline__ unsigned long long res_gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t res_smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ bool res_mbar_wait(uint32_t bar, uint32_t parity, unsigned long long timeout_ns)
+{
+    const unsigned long long t0 = res_gtimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (res_gtimer() - t0 > timeout_ns) return false;
+    }
+}
+
+__global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = int(cluster.num_blocks());
+    const int rank = int(cluster.block_rank());
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *tabs = reinterpret_cast<uint32_t *>(smem + kOffTabs);
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(smem + kOffCtrl);
+    const uint32_t bar = res_smem_u32(smem + kOffBar);
+    uint8_t *rows_base = smem + kOffRows;
+
+    for (int i = tid; i < 256; i += blockDim.x) {
+        tabs[i] = d_res_point_table.v[i];
+        tabs[256 + i] = d_res_component_table.v[i];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t bar_parity = 0;
+    __syncthreads();
+
+    for (;;) {
+        if (rank == 0 && tid == 0) ctrl->job = int(atomicAdd(&P.ctl->next_job, 1u));
+        cluster.sync();
+        const int job = cluster.map_shared_rank(ctrl, 0)->job;
+        cluster.sync();  // every block has read the leader's word before it may leave or overwrite it
+        if (job >= P.njobs) break;
+        const ResJob J = P.jobs[job];
+        const int es = J.dtype == THIN_U16 ? 2 : 1;
+        const int R = J.rows, RP = J.rp, CW = J.cw, WPR = J.wpr;
+        const int CR = R / 2;
+        const int slot_words = CR * WPR;
+        uint32_t *bits = reinterpret_cast<uint32_t *>(smem + res_bits_off(R, RP));
+        uint16_t *queue = reinterpret_cast<uint16_t *>(smem + res_queue_off(R, RP, WPR));
+        const int row0 = rank * R;
+        const int nrows = max(0, min(R, J.h - row0));
+        const int rowb = J.w * es;
+        const char *gimg = reinterpret_cast<const char *>(J.img);
+
+        // ---- stage this block's rows
+        if (J.bulk && nrows > 0) {
+            if (tid == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                             "r"(uint32_t(nrows * rowb))
+                             : "memory");
+            __syncthreads();
+            for (int r = tid; r < nrows; r += blockDim.x) {
+                const uint32_t dst = res_smem_u32(rows_base + size_t(r) * RP + 16);
+                const char *src = gimg + size_t(row0 + r) * J.pitch;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                    "l"(src), "r"(uint32_t(rowb)), "r"(bar)
+                    : "memory");
+            }
+            if (!res_mbar_wait(bar, bar_parity, P.timeout_ns)) {
+                if (tid == 0) atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
+                res_mbar_wait(bar, bar_parity, P.timeout_ns);  // let copies in flight land (bounded)
+            }
+            bar_parity ^= 1u;
+        } else {
+            for (int e = tid; e < nrows * rowb; e += blockDim.x) {
+                const int r = e / rowb, c = e - r * rowb;
+                rows_base[size_t(r) * RP + 16 + c] = uint8_t(gimg[size_t(row0 + r) * J.pitch + c]);
+            }
+        }
+        for (int i = tid; i < 4 * slot_words; i += blockDim.x) bits[i] = 0u;
+        if (tid == 0) {
+            ctrl->qn[0] = 0;
+            ctrl->qn[1] = 0;
+            ctrl->last = -1;
+            ctrl->nlow = 0;
+        }
+        if (tid < 8) ctrl->peer_last[tid] = -1;
+        cluster.sync();  // every block's rows are in place before anyone reads a neighbour's
+
+        const uint8_t *rows_up = rank > 0 ? cluster.map_shared_rank(rows_base, rank - 1) : nullptr;
+        const uint8_t *rows_down = rank + 1 < C ? cluster.map_shared_rank(rows_base, rank + 1) : nullptr;
+        const uint32_t *bits_up = rank > 0 ? cluster.map_shared_rank(bits, rank - 1) : nullptr;
+        const uint32_t *bits_down = rank + 1 < C ? cluster.map_shared_rank(bits, rank + 1) : nullptr;
+        uint32_t *rec = reinterpret_cast<uint32_t *>(smem + res_rec_off(R, RP, WPR)) + WPR;  // rows -1 .. CR
+        const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
+        const uint32_t Mcw = CW > 1 ? 0xffffffffu / uint32_t(CW) + 1u : 0u;
+        const uint32_t *comp = tabs + 256;
+
+        long long g = P.start_phase;
+        int converged = 0;
+        int nlow = 0;
+        for (;;) {
+            const long long rel = g - P.start_phase;
+            if (P.max_phases >= 0 && rel >= P.max_phases) break;
+            const int p = int(g & 3), px = p & 1, py = p >> 1;
+            const int cur = p;  // bitmap slot of this phase's changes
+            const int s1 = int((g - 1) & 3) * slot_words, s2 = int((g - 2) & 3) * slot_words,
+                      s3 = int((g - 3) & 3) * slot_words;
+            const int qi = int(g & 1);
+            // 1a. cells that changed in phases g-3 .. g-1, one cell row beyond each edge
+            if (rel > 3) {
+                for (int wi = tid; wi < slot_words + 2 * WPR; wi += blockDim.x) {
+                    const int w2 = wi - WPR;  // word index relative to this block's first cell row
+                    uint32_t v = 0;
+                    if (w2 < 0) {
+                        if (bits_up) v = bits_up[s1 + slot_words + w2] | bits_up[s2 + slot_words + w2] | bits_up[s3 + slot_words + w2];
+                    } else if (w2 >= slot_words) {
+                        if (bits_down) v = bits_down[s1 + w2 - slot_words] | bits_down[s2 + w2 - slot_words] | bits_down[s3 + w2 - slot_words];
+                    } else {
+                        v = bits[s1 + w2] | bits[s2 + w2] | bits[s3 + w2];
+                    }
+                    rec[w2] = v;
+                }
+                __syncthreads();
+            }
+            // 1b. dirty cells of this phase (3 x 3 dilation) -> queue
+            for (int wb = warp * 32; wb < slot_words; wb += blockDim.x) {
+                const int wi = wb + lane;
+                uint32_t d = 0;
+                if (wi < slot_words) {
+                    const int cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
+                    const int i = wi - cr * WPR;
+                    const int y = row0 + 2 * cr + py;
+                    if (y >= 1 && y <= J.h - 2) {
+                        const int valid = CW - 32 * i;
+                        const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+                        if (rel <= 3) {
+                            d = vmask;
+                        } else {
+                            const uint32_t *rp0 = rec + cr * WPR + i;
+                            const uint32_t a1 = rp0[-WPR] | rp0[0] | rp0[WPR];
+                            const uint32_t a0 = i > 0 ? rp0[-WPR - 1] | rp0[-1] | rp0[WPR - 1] : 0u;
+                            const uint32_t a2 = i + 1 < WPR ? rp0[-WPR + 1] | rp0[1] | rp0[WPR + 1] : 0u;
+                            d = (a1 | (a1 << 1) | (a0 >> 31) | (a1 >> 1) | (a2 << 31)) & vmask;
+                        }
+                    }
+                    bits[cur * slot_words + wi] = 0u;  // this slot held phase g-4
+                }
+                const int cnt = __popc(d);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int base = 0;
+                if (lane == 31 && total) base = atomicAdd(&ctrl->qn[qi], total);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                int pos = base + incl - cnt;
+                if (d) {
+                    const int cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
+                    const int i = wi - cr * WPR;
+                    while (d) {
+                        const int b = __ffs(d) - 1;
+                        d &= d - 1;
+                        queue[pos++] = uint16_t(cr * CW + 32 * i + b);
+                    }
+                }
+            }
+            if (tid == 0) ctrl->qn[qi ^ 1] = 0;  // the next phase's counter
+            __syncthreads();
+            const int qn = ctrl->qn[qi];
+            // 2. test and lower the queued groups
+            bool moved_any = false;
+            for (int k = tid; k < qn; k += blockDim.x) {
+                const int code = queue[k];
+                const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
+                const int cc = code - cr * CW;
+                const int lr = 2 * cr + py;
+                uint32_t vm = 0;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int x = 8 * cc + px + 2 * kk;
+                    vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
+                }
+                const size_t off = 16 + size_t(8 * es) * cc;
+                uint8_t *rb = rows_base + size_t(lr) * RP + off;
+                const uint8_t *ra = lr > 0 ? rb - RP : rows_up + size_t(R - 1) * RP + off;
+                const uint8_t *rc = lr + 1 < R ? rb + RP : rows_down + off;
+                uint32_t moved;
+                if (es == 1)
+                    moved = item_u8(ra, rb, rc, px, vm, vm, comp, J.lam, P.rule, nlow);
+                else
+                    moved = item_u16(reinterpret_cast<const uint16_t *>(ra), reinterpret_cast<uint16_t *>(rb),
+                                     reinterpret_cast<const uint16_t *>(rc), px, vm, vm, tabs, J.lam, P.rule, nlow);
+                if (moved) {
+                    atomicOr(&bits[cur * slot_words + cr * WPR + (cc >> 5)], 1u << (cc & 31));
+                    moved_any = true;
+                }
+            }
+            if (__syncthreads_or(moved_any) && tid == 0) ctrl->last = g;
+            __syncthreads();
+            if (tid < C) cluster.map_shared_rank(ctrl, tid)->peer_last[rank] = ctrl->last;  // push to every block
+            cluster.sync();  // phase g done everywhere
+            long long lc = -1;
+            for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+            ++g;
+            if (g - P.start_phase >= 4 && lc < g - 3) {  // three quiet phases: fixed point
+                converged = 1;
+                break;
+            }
+        }
+        // ---- results
+        nlow = __reduce_add_sync(0xffffffffu, nlow);
+        if (lane == 0 && nlow) atomicAdd(&ctrl->nlow, (unsigned long long)nlow);
+        __syncthreads();
+        {
+            const int ra = max(row0, 1), rb = min(row0 + nrows, J.h - 1);  // border rows never change
+            char *gout = reinterpret_cast<char *>(J.img);
+            if (J.bulk) {
+                const int vpr = rowb / 16;
+                for (int e = tid; e < (rb - ra) * vpr; e += blockDim.x) {
+                    const int r = e / vpr, c = e - r * vpr;
+                    *reinterpret_cast<uint4 *>(gout + size_t(ra + r) * J.pitch + 16 * c) =
+                        *reinterpret_cast<const uint4 *>(rows_base + size_t(ra + r - row0) * RP + 16 + 16 * c);
+                }
+            } else {
+                for (int e = tid; e < (rb - ra) * rowb; e += blockDim.x) {
+                    const int r = e / rowb, c = e - r * rowb;
+                    gout[size_t(ra + r) * J.pitch + c] = char(rows_base[size_t(ra + r - row0) * RP + 16 + c]);
+                }
+            }
+        }
+        if (tid == 0) {
+            ResStat &S = P.st[job];
+            atomicAdd(&S.lowered, ctrl->nlow);
+            if (rank == 0) {
+                long long lc = -1;
+                for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+                S.last_change = lc;
+                S.phases = g - P.start_phase;
+                S.converged = converged;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the next bulk copy
+        cluster.sync();  // nobody reads this job's rows or control words any more
+    }
+}
+
+}  // namespace
+
+// Smallest cluster (1, 2, 4, 8 blocks) whose shared memory holds the image; 0 if none.
+int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_out, int *rp_out)
+{
+    const int es = dtype == THIN_U16 ? 2 : 1;
+    const int rp = int((size_t(w) * es + 15) / 16 * 16) + 32;
+    const int cw = (w + 7) / 8, wpr = (cw + 31) / 32;
+    for (int C = 1; C <= 8; C *= 2) {
+        int rows = (h + C - 1) / C;
+        rows += rows & 1;
+        if (rows / 2 * cw > 65535) continue;  // queue codes are 16-bit
+        if (res_smem_bytes(rows, rp, cw, wpr) <= smem_limit) {
+            if (rows_out) *rows_out = rows;
+            if (rp_out) *rp_out = rp;
+            return C;
+        }
+    }
+    return 0;
+}
+
+size_t resident_smem_limit()
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return size_t(optin > 0 ? optin : 48 * 1024);
+}
+
+// Runs the jobs (all fitting cluster size C) in one launch of k_resident.
+int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    if (n <= 0) return THIN_OK;
+    if (opt.max_phases == 0) {
+        if (out)
+            for (int k = 0; k < n; ++k) {
+                std::memset(&out[k], 0, sizeof out[k]);
+                out[k].status = THIN_ERR_NOT_CONVERGED;
+                out[k].last_change_phase = -1;
+                out[k].end_phase = opt.start_phase;
+            }
+        return THIN_ERR_NOT_CONVERGED;
+    }
+    const size_t limit = resident_smem_limit();
+    std::vector<ResJob> rj(n);
+    size_t smem = 0;
+    for (int k = 0; k < n; ++k) {
+        const JobSpec &J = jobs[k];
+        ResJob &r = rj[k];
+        std::memset(&r, 0, sizeof r);
+        const int es = elem_size(J.dtype);
+        r.img = reinterpret_cast<unsigned long long>(J.img);
+        r.pitch = J.pitch;
+        r.w = J.w;
+        r.h = J.h;
+        r.dtype = J.dtype;
+        r.lam = J.lam;
+        int rows = (J.h + C - 1) / C;
+        rows += rows & 1;
+        r.rows = rows;
+        r.rp = int((size_t(J.w) * es + 15) / 16 * 16) + 32;
+        r.cw = (J.w + 7) / 8;
+        r.wpr = (r.cw + 31) / 32;
+        r.bulk = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0) && ((size_t(J.w) * es) % 16 == 0);
+        r.index = k;
+        const size_t need = res_smem_bytes(r.rows, r.rp, r.cw, r.wpr);
+        if (need > limit || r.rows / 2 * r.cw > 65535) return THIN_ERR_ARG;
+        smem = std::max(smem, need);
+    }
+    // longest-first: larger lambda and larger images tend to run longer
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double ca = double(rj[a].w) * rj[a].h * (1.0 + rj[a].lam), cb = double(rj[b].w) * rj[b].h * (1.0 + rj[b].lam);
+        return ca > cb;
+    });
+    std::vector<ResJob> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = rj[order[k]];
+
+    const size_t o_jobs = 0;
+    const size_t o_st = (sizeof(ResJob) * n + 255) / 256 * 256;
+    const size_t o_ctl = o_st + (sizeof(ResStat) * n + 255) / 256 * 256;
+    const size_t total = o_ctl + 256;
+    char *base = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&base), total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return THIN_ERR_OOM;
+    }
+    std::vector<ResStat> st0(n);
+    for (auto &s : st0) {
+        std::memset(&s, 0, sizeof s);
+        s.last_change = -1;
+    }
+    ResCtl ctl0;
+    std::memset(&ctl0, 0, sizeof ctl0);
+    cudaError_t e = cudaMemcpyAsync(base + o_jobs, sorted.data(), sizeof(ResJob) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_st, st0.data(), sizeof(ResStat) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
+
+    ResArgs P;
+    std::memset(&P, 0, sizeof P);
+    P.jobs = reinterpret_cast<const ResJob *>(base + o_jobs);
+    P.st = reinterpret_cast<ResStat *>(base + o_st);
+    P.ctl = reinterpret_cast<ResCtl *>(base + o_ctl);
+    P.njobs = n;
+    P.rule = opt.rule;
+    P.start_phase = opt.start_phase;
+    P.max_phases = opt.max_phases;
+    P.timeout_ns = 2000000000ull;
+    if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
+
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kResThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(C);
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_resident, &cfg);
+    }
+    if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(C * std::min(clusters, n));
+        e = cudaLaunchKernelEx(&cfg, k_resident, P);
+    }
+    int rc = THIN_OK;
+    if (e == cudaSuccess && out) {
+        std::vector<ResStat> st(n);
+        ResCtl ctl;
+        e = cudaMemcpyAsync(st.data(), P.st, sizeof(ResStat) * n, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < n; ++k) {
+                const ResStat &S = st[k];
+                thin_stats &o = out[sorted[k].index];
+                std::memset(&o, 0, sizeof o);
+                o.converged = S.converged && !ctl.error;
+                o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
+                o.phases = S.phases;
+                o.lowered = (int64_t)S.lowered;
+                o.last_change_phase = S.last_change;
+                o.end_phase = opt.start_phase + S.phases;
+                o.tiles_visited = 0;
+                o.steps = S.phases;
+                if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
+            }
+        }
+    }
+    cudaFreeAsync(base, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return rc;
+}
+
+}  // namespace thin

@@ -1,0 +1,198 @@
+// thin_simd.cuh -- the point test of Sec. 2.1 and the lowering loop of
+// Sec. 2.2 on four points of one parity at once, shared by the engines.
+//
+// A work item is the four points (x0 + px + 2k, y), k = 0..3, of one parity in
+// an 8-pixel aligned block of row y.  The callers pass pointers to that block
+// in rows y - 1, y and y + 1 (any of them may live in another block's shared
+// memory); the rows must hold readable pixels from 1 pixel left to 1 pixel
+// right of the block (u8: the aligned words just left and right of it).
+#pragma once
+
+#include <cstdint>
+
+#include "thin_common.cuh"
+
+namespace thin {
+
+constexpr uint32_t kMsb8 = 0x80808080u;
+constexpr uint32_t kLsb8 = 0x01010101u;
+
+// Four unsigned byte comparisons a < b at once: bit 7 of each byte of the
+// result is set where byte(a) < byte(b); all other bits are 0.
+// bl = b & 0x7f7f7f7f, bh = b & 0x80808080.  The subtraction of the low
+// seven bits cannot borrow across bytes; bit 7 is then fixed up by hand.
+__device__ __forceinline__ uint32_t lt8(uint32_t a, uint32_t b, uint32_t bl, uint32_t bh)
+{
+    const uint32_t x = a ^ b;
+    const uint32_t r = (a | kMsb8) - bl;
+    const uint32_t dh = (r ^ ~x) & kMsb8;  // bit 7 of the true byte difference a - b
+    return (x & bh) | (~x & dh);           // borrow out of the byte
+}
+
+// 0xff in each byte whose bit 7 is set, else 0x00 (prmt sign replication).
+__device__ __forceinline__ uint32_t msb_to_mask(uint32_t v)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xba98;" : "=r"(r) : "r"(v));
+    return r;
+}
+
+// Rotations of each byte seen as the 8-ring of neighbour bits:
+// rot_prev puts bit i-1 at bit i, rot_next puts bit i+1 at bit i.
+__device__ __forceinline__ uint32_t rot_prev(uint32_t v) { return ((v << 1) & 0xfefefefeu) | ((v >> 7) & kLsb8); }
+__device__ __forceinline__ uint32_t rot_next(uint32_t v) { return ((v >> 1) & 0x7f7f7f7fu) | ((v << 7) & kMsb8); }
+
+// Bit 7 set in every nonzero byte.
+__device__ __forceinline__ uint32_t nonzero8(uint32_t v) { return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) & kMsb8; }
+
+// Merge eight per-direction comparison results (bit 7 per byte) into the
+// ring mask of each point (byte k = mask of point k, bit d = direction d).
+__device__ __forceinline__ uint32_t merge_dirs(const uint32_t lt[8])
+{
+    return (lt[0] >> 7) | (lt[1] >> 6) | (lt[2] >> 5) | (lt[3] >> 4) | (lt[4] >> 3) | (lt[5] >> 2) |
+           (lt[6] >> 1) | lt[7];
+}
+
+// The lowering loop of Sec. 2.2 on four points of one parity at once (bytes
+// of `c`), neighbours fixed (bytes of nb[d], ring order E, NE, N, NW, W, SW,
+// S, SE).  For each point: Gamma^-- is its lower-neighbour mask M; T-- is the
+// number of runs of M once isolated lower corners (those with no lower
+// 4-neighbour beside them, never 4-adjacent to x) are dropped; under (8,4),
+// T+ = T-- except when no 4-neighbour is lower (T-- = 0) or all eight are
+// (T+ = 0), so "destructible" is "exactly one run start".  k-divergent points
+// (two or more runs) are lambda-destructible when at most one of their
+// counted components fails F(x) - F^-(c) <= lambda.  `vm` has 0x01 in the
+// bytes of points that may move.  Returns the bytes lowered (0x01 each) over
+// all iterations; `c` receives the new values, `nin` the lowering steps of the
+// points also in `in`.  `comp` is the component-mask table.
+__device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
+                                           const uint32_t *comp, uint32_t lam, int rule, int &nin)
+{
+    uint32_t okacc = 0;
+#pragma unroll 1
+    for (int it = 0; it < 9; ++it) {
+        const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
+        uint32_t lt[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) lt[d] = lt8(nb[d], c, bl, bh);
+        const uint32_t M = merge_dirs(lt);
+        const uint32_t iso = M & 0xaaaaaaaau & ~rot_prev(M) & ~rot_next(M);
+        const uint32_t mc = M ^ iso;                              // counted lower neighbours
+        const uint32_t st = mc & ~rot_prev(mc);                   // starts of their runs
+        const uint32_t t = st & ((st | kMsb8) - kLsb8);           // starts minus the lowest one
+        const uint32_t nzt = nonzero8(t);
+        uint32_t ok = ((nonzero8(st) & ~nzt) >> 7) & vm;          // destructible
+        const uint32_t dv = (nzt >> 7) & vm;                      // k-divergent
+        if (lam != 0 && dv) {
+            // deep lower neighbours: value < F(x) - lambda (none when F(x) <= lambda)
+            const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
+            const uint32_t cl = __vsubus4(c, lrep);
+            const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
+            uint32_t dp[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
+            const uint32_t deep = merge_dirs(dp) & mc;
+            // F^- = max: a component fails when no member is shallow (value >= F(x) - lambda);
+            // F^- = min: a component fails when some member is deep
+            const uint32_t probe = rule == 0 ? (mc & ~deep) : deep;
+            uint32_t okdv = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t e = comp[(M >> (8 * k)) & 0xffu];  // component masks, one per byte
+                const uint32_t hit = __popc(nonzero8(e & (((probe >> (8 * k)) & 0xffu) * kLsb8)));
+                const uint32_t bad = rule == 0 ? __popc(nonzero8(e)) - hit : hit;
+                okdv |= (bad <= 1 ? 1u : 0u) << (8 * k);
+            }
+            ok |= okdv & dv;
+        }
+        if (!ok) break;
+        // alpha^-: largest lower neighbour, by a tree of byte maxima; direction d
+        // of point k is lower iff bit d of byte k of M is set
+#define THIN_LOWER_NB(d) (nb[d] & ((((M >> (d)) & kLsb8) * 0xffu)))
+        const uint32_t alpha =
+            __vmaxu4(__vmaxu4(__vmaxu4(THIN_LOWER_NB(0), THIN_LOWER_NB(1)), __vmaxu4(THIN_LOWER_NB(2), THIN_LOWER_NB(3))),
+                     __vmaxu4(__vmaxu4(THIN_LOWER_NB(4), THIN_LOWER_NB(5)), __vmaxu4(THIN_LOWER_NB(6), THIN_LOWER_NB(7))));
+#undef THIN_LOWER_NB
+        const uint32_t okm = ok * 0xffu;
+        c = (alpha & okm) | (c & ~okm);
+        okacc |= ok;
+        nin += __popc(ok & in);
+    }
+    return okacc;
+}
+
+// One u8 work item.  ra, rb, rc point at the 8-byte aligned block in rows
+// y - 1, y, y + 1; the words at -4 and +8 of each must be readable.
+__device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
+                                            uint32_t in, const uint32_t *comp, uint32_t lam, int rule, int &nin)
+{
+    const uint2 wa = *reinterpret_cast<const uint2 *>(ra);
+    const uint2 wb = *reinterpret_cast<const uint2 *>(rb);
+    const uint2 wc = *reinterpret_cast<const uint2 *>(rc);
+    const uint32_t Ea = __byte_perm(wa.x, wa.y, 0x6420), Oa = __byte_perm(wa.x, wa.y, 0x7531);
+    const uint32_t Eb = __byte_perm(wb.x, wb.y, 0x6420), Ob = __byte_perm(wb.x, wb.y, 0x7531);
+    const uint32_t Ec = __byte_perm(wc.x, wc.y, 0x6420), Oc = __byte_perm(wc.x, wc.y, 0x7531);
+    uint32_t nb[8], c;
+    if (px == 0) {
+        const uint32_t La = *reinterpret_cast<const uint32_t *>(ra - 4);
+        const uint32_t Lb = *reinterpret_cast<const uint32_t *>(rb - 4);
+        const uint32_t Lc = *reinterpret_cast<const uint32_t *>(rc - 4);
+        c = Eb;
+        nb[0] = Ob;
+        nb[1] = Oa;
+        nb[2] = Ea;
+        nb[3] = __byte_perm(La, Oa, 0x6543);
+        nb[4] = __byte_perm(Lb, Ob, 0x6543);
+        nb[5] = __byte_perm(Lc, Oc, 0x6543);
+        nb[6] = Ec;
+        nb[7] = Oc;
+    } else {
+        const uint32_t Ra = *reinterpret_cast<const uint32_t *>(ra + 8);
+        const uint32_t Rb = *reinterpret_cast<const uint32_t *>(rb + 8);
+        const uint32_t Rc = *reinterpret_cast<const uint32_t *>(rc + 8);
+        c = Ob;
+        nb[0] = __byte_perm(Eb, Rb, 0x4321);
+        nb[1] = __byte_perm(Ea, Ra, 0x4321);
+        nb[2] = Oa;
+        nb[3] = Ea;
+        nb[4] = Eb;
+        nb[5] = Ec;
+        nb[6] = Oc;
+        nb[7] = __byte_perm(Ec, Rc, 0x4321);
+    }
+    const uint32_t moved = lower4(c, nb, vm, in, comp, lam, rule, nin);
+    if (moved) {
+        uint2 out;
+        if (px == 0)
+            out = make_uint2(__byte_perm(c, Ob, 0x5140), __byte_perm(c, Ob, 0x7362));
+        else
+            out = make_uint2(__byte_perm(Eb, c, 0x5140), __byte_perm(Eb, c, 0x7362));
+        *reinterpret_cast<uint2 *>(rb) = out;
+    }
+    return moved;
+}
+
+// One u16 work item: the same four points, one at a time through the point
+// table.  ra, rb, rc point at the block's first pixel in rows y - 1, y, y + 1.
+__device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px,
+                                             uint32_t vm, uint32_t in, const uint32_t *tab, uint32_t lam, int rule,
+                                             int &nin)
+{
+    uint32_t moved = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        if (!((vm >> (8 * k)) & 1u)) continue;
+        const int x = px + 2 * k;
+        uint32_t nb[8] = {rb[x + 1], ra[x + 1], ra[x], ra[x - 1], rb[x - 1], rc[x - 1], rc[x], rc[x + 1]};
+        int nl = 0;
+        const uint32_t c2 = lower_point(rb[x], nb, tab, lam, rule, nl);
+        if (nl) {
+            rb[x] = static_cast<uint16_t>(c2);
+            moved |= 1u << (8 * k);
+            if ((in >> (8 * k)) & 1u) nin += nl;
+        }
+    }
+    return moved;
+}
+
+}  // namespace thin

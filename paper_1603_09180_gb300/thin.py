@@ -32,7 +32,7 @@ ERRORS = {THIN_ERR_ARG: "bad argument", THIN_ERR_UNSUPPORTED: "unsupported", THI
 U8, U16 = 0, 1
 ADJ_8_4, ADJ_4_8 = 0, 1
 RULE_MAX, RULE_MIN = 0, 1
-KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED, KERNEL_RESIDENT = 0, 1, 2, 3
 
 
 class ThinError(RuntimeError):
@@ -103,7 +103,8 @@ def options(rule=RULE_MAX, kernel=KERNEL_AUTO, tile=None, halo=0, start_phase=0,
     o = Options()
     load().thin_default_options(ctypes.byref(o))
     o.rule = {"max": RULE_MAX, "min": RULE_MIN}.get(rule, rule)
-    o.kernel = {"auto": KERNEL_AUTO, "naive": KERNEL_NAIVE, "tiled": KERNEL_TILED}.get(kernel, kernel)
+    o.kernel = {"auto": KERNEL_AUTO, "naive": KERNEL_NAIVE, "tiled": KERNEL_TILED,
+                "resident": KERNEL_RESIDENT}.get(kernel, kernel)
     if tile is not None:
         o.tile_w, o.tile_h = (tile, tile) if isinstance(tile, int) else tile
     o.halo = halo or 0

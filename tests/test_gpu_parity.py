@@ -49,11 +49,12 @@ def test_naive_matches_oracle(shape, lam):
     check(img, lam, kernel="naive")
 
 
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("lam", [0, 5, 20])
-def test_tiled_default_matches_oracle(shape, lam):
+def test_engines_match_oracle(shape, lam, kernel):
     img = synth.value_noise_image(*shape, "u8", seed=shape[0] * 3 + shape[1])
-    check(img, lam)
+    check(img, lam, kernel=kernel)
 
 
 @pytest.mark.parametrize("tile,halo", [((16, 8), 3), ((16, 16), 4), ((32, 16), 8), ((48, 40), 5), ((64, 64), 8),
@@ -62,36 +63,39 @@ def test_tiled_default_matches_oracle(shape, lam):
 def test_tiled_tile_shapes(tile, halo, dt):
     img = synth.value_noise_image(150, 170, dt, seed=halo * 11 + tile[0])
     lam = 7 if dt == "u8" else 100
-    check(img, lam, tile=tile, halo=halo)
+    check(img, lam, tile=tile, halo=halo, kernel="tiled")
 
 
 @pytest.mark.parametrize("rule", ["max", "min"])
-@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+@pytest.mark.parametrize("kernel", ["naive", "tiled", "resident"])
 def test_rules(rule, kernel):
     img = synth.value_noise_image(90, 110, "u8", seed=31)
     check(img, 12, rule=rule, kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
 @pytest.mark.parametrize("dt,vmax,lam", [("u16", 4095, 0), ("u16", 4095, 30), ("u16", 65535, 700), ("u8", 255, 255)])
-def test_value_ranges(dt, vmax, lam):
+def test_value_ranges(dt, vmax, lam, kernel):
     img = synth.value_noise_image(96, 120, dt, seed=vmax + lam, vmax=vmax)
-    check(img, lam)
+    check(img, lam, kernel=kernel)
 
 
-def test_white_noise_worst_case():
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_white_noise_worst_case(kernel):
     img = synth.uniform_noise_image(130, 150, "u8", seed=4)
-    check(img, 0)
-    check(img, 40)
+    check(img, 0, kernel=kernel)
+    check(img, 40, kernel=kernel)
 
 
-def test_unaligned_pitch_and_offset():
-    """Images whose rows are not 16-byte aligned go through internal buffers."""
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_unaligned_pitch_and_offset(kernel):
+    """Rows that are not 16-byte aligned: internal buffers (tiled) or plain loads (resident)."""
     img = synth.value_noise_image(70, 90, "u8", seed=2)
     big = np.zeros((80, 101), np.uint8)
     big[3:73, 5:95] = img
     t = to_dev(big)
     view = t[3:73, 5:95]
-    st = thin.run(view, 9)
+    st = thin.run(view, 9, kernel=kernel)
     torch.cuda.synchronize()
     ref, _ = oracle.thin(img, 9)
     out = to_host(t)
@@ -102,7 +106,7 @@ def test_unaligned_pitch_and_offset():
     assert st["converged"] == 1
 
 
-@pytest.mark.parametrize("kernel", ["naive", "tiled"])
+@pytest.mark.parametrize("kernel", ["naive", "tiled", "resident"])
 @pytest.mark.parametrize("cap", [1, 4, 7, 13, 40])
 def test_cap_and_resume(kernel, cap):
     img = synth.value_noise_image(80, 96, "u8", seed=12)
@@ -120,13 +124,15 @@ def test_cap_and_resume(kernel, cap):
     assert st["lowered"] + st2["lowered"] == oracle.thin(img, 10)[1]["lowered"]
 
 
-def test_start_phase_offsets():
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_start_phase_offsets(kernel):
     img = synth.value_noise_image(60, 75, "u8", seed=8)
     for g in (1, 2, 3, 6):
-        check(img, 4, start_phase=g)
+        check(img, 4, start_phase=g, kernel=kernel)
 
 
-def test_batch_mixed_equals_alone():
+@pytest.mark.parametrize("kernel", ["auto", "tiled"])
+def test_batch_mixed_equals_alone(kernel):
     rng = np.random.default_rng(0)
     imgs, lams, refs = [], [], []
     for k in range(14):
@@ -137,8 +143,13 @@ def test_batch_mixed_equals_alone():
         imgs.append(img)
         lams.append(lam)
         refs.append(oracle.thin(img, lam))
+    if kernel == "auto":  # one image too large for a cluster's shared memory: both engines in one call
+        big = synth.value_noise_image(1000, 2100, "u8", seed=99)
+        imgs.append(big)
+        lams.append(0)
+        refs.append(oracle.thin(big, 0))
     ts = [to_dev(a) for a in imgs]
-    sts, rc = thin.batch(ts, lams)
+    sts, rc = thin.batch(ts, lams, kernel=kernel)
     torch.cuda.synchronize()
     assert rc == 0
     for t, (ref, rst), st in zip(ts, refs, sts):
@@ -157,11 +168,25 @@ def test_deterministic_repeats():
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
-def test_config1_full_size():
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_config1_full_size(kernel):
     """512 x 512 u8, lambda = 0, seed 1603: bit-exact at full size."""
     img = synth.value_noise_image(512, 512, "u8", seed=1603)
-    st, rst = check(img, 0)
-    assert st["tiles_visited"] > 0
+    check(img, 0, kernel=kernel)
+
+
+@pytest.mark.parametrize("shape,dt,lam", [((200, 300), "u8", 9), ((512, 512), "u8", 5), ((700, 700), "u8", 0),
+                                          ((1024, 1024), "u8", 0), ((512, 512), "u16", 0), ((333, 250), "u16", 7)])
+def test_resident_cluster_sizes(shape, dt, lam):
+    """Images that need 1, 2, 4 and 8 blocks per cluster, alone and in a batch."""
+    img = synth.value_noise_image(*shape, dt, seed=shape[0] + shape[1])
+    check(img, lam, kernel="resident")
+    ref, rst = oracle.thin(img, lam)
+    ts = [to_dev(img) for _ in range(3)]
+    sts, rc = thin.batch(ts, [lam] * 3, kernel="resident")
+    torch.cuda.synchronize()
+    for t, st in zip(ts, sts):
+        assert np.array_equal(to_host(t), ref) and st["lowered"] == rst["lowered"]
 
 
 def test_timeout_reports_status_and_context_survives(monkeypatch):
@@ -171,8 +196,8 @@ def test_timeout_reports_status_and_context_survives(monkeypatch):
     monkeypatch.setenv("THIN_TIMEOUT_NS", "50000000")
     img = synth.value_noise_image(200, 200, "u8", seed=1)
     t = to_dev(img)
-    st = thin.run(t, 0, debug=1, check=False)
+    st = thin.run(t, 0, debug=1, check=False, kernel="tiled")
     torch.cuda.synchronize()
     assert st["rc"] == thin.THIN_ERR_TIMEOUT and st["status"] == thin.THIN_ERR_TIMEOUT
     monkeypatch.delenv("THIN_TIMEOUT_NS")
-    check(img, 0)
+    check(img, 0, kernel="tiled")

@@ -42,7 +42,8 @@ def test_noalloc_matches_thin_run_on_two_calls_in_a_row():
         if img.dtype == np.uint16:
             ref = ref.view(torch.uint16)
         base = ref.clone()
-        rc0, st0 = _call(lib.thin_run, ref, lam)
+        # thin_run_noalloc is the tiled engine: compare with thin_run on that engine
+        rc0, st0 = _call(lib.thin_run, ref, lam, thin.options(kernel="tiled"))
         assert rc0 == thin.THIN_OK
         for _ in range(2):  # the second call finds the first call's leftovers in the scratch array
             t = base.clone()
@@ -59,7 +60,7 @@ def test_noalloc_unaligned_rows_and_cap():
     big = torch.zeros((110, 141), dtype=torch.uint8, device="cuda")
     big[4:104, 3:133] = torch.from_numpy(img).cuda()
     ref = big.clone()
-    o = thin.options(max_phases=13)
+    o = thin.options(max_phases=13, kernel="tiled")
     rc0, st0 = _call(lib.thin_run, ref[4:104, 3:133], 9, o)
     rc, st = _call(lib.thin_run_noalloc, big[4:104, 3:133], 9, o)
     assert rc == rc0 and st["end_phase"] == st0["end_phase"] == 13
