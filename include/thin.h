@@ -93,6 +93,9 @@ typedef struct {
     int64_t end_phase;         /* global phase index to resume from */
     int64_t tiles_visited;     /* tile visits of the tiled kernel (0 for NAIVE) */
     int64_t steps;             /* tile steps (tiled) or rounds of four phases (naive) */
+    int64_t tested;            /* point tests made: a point is tested in a phase of its parity only
+                                  if a neighbour moved since its last test (all points in the first
+                                  four phases); the work behind the sweep rate */
 } thin_stats;
 
 /* Fills *opt with the defaults (rule MAX, AUTO kernel, default tiles, phase 0, no cap). */

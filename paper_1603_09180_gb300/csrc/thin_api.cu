@@ -64,11 +64,15 @@ int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStrea
     for (int C = 1; C <= 8; C *= 2) {
         std::vector<JobSpec> group;
         std::vector<int> where;
-        for (int k = 0; k < n; ++k)
-            if (cls[k] > 0 && std::max(cls[k], spread) == C) {
+        for (int k = 0; k < n; ++k) {
+            if (cls[k] <= 0) continue;
+            int c = cls[k];  // spread, but keep at least 32 rows per block
+            while (c < spread && specs[k].h / (2 * c) >= 32) c *= 2;
+            if (c == C) {
                 group.push_back(specs[k]);
                 where.push_back(k);
             }
+        }
         if (group.empty()) continue;
         std::vector<thin_stats> st(out ? group.size() : 0);
         const int r = resident_run(group.data(), int(group.size()), C, o, s, out ? st.data() : nullptr);

@@ -117,6 +117,15 @@ int naive_run(const JobSpec &job, const thin_options &opt, cudaStream_t stream, 
         out->end_phase = g;
         out->tiles_visited = 0;
         out->steps = rounds;
+        // every interior point of the phase's parity is tested in every phase
+        long long per[4] = {0, 0, 0, 0};
+        for (int p = 0; p < 4; ++p) {
+            const long long nx = (job.w - 2 - ((p & 1) ? 1 : 2)) / 2 + 1, ny = (job.h - 2 - ((p >> 1) ? 1 : 2)) / 2 + 1;
+            per[p] = (nx > 0 && ny > 0) ? nx * ny : 0;
+        }
+        long long t = 0;
+        for (long long q = opt.start_phase; q < g; ++q) t += per[q & 3];
+        out->tested = t;
     }
     return status;
 }

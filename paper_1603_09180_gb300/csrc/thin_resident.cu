@@ -36,6 +36,7 @@ namespace thin {
 namespace {
 
 constexpr int kResThreads = 1024;
+constexpr int kResStep = 8;  // phases between halo exchanges = halo rows held from each neighbour
 
 struct ResJob {
     unsigned long long img;    // the caller's image, thinned in place
@@ -48,11 +49,13 @@ struct ResJob {
     int wpr;    // bitmap words per cell row = ceil(cw / 32)
     int bulk;   // rows are 16-byte aligned and a multiple of 16 bytes: stage them by bulk copy
     int index;  // position of the job in the caller's list
-    int pad0, pad1;
+    int hr;     // halo rows copied from each neighbouring block (even; 0 for a one-block cluster)
+    int steph;  // phases between exchanges of halo rows
 };
 
 struct ResStat {
     unsigned long long lowered;
+    unsigned long long tested;   // point tests on own rows
     long long last_change;  // global phase index, -1 if none
     long long phases;
     int converged;
@@ -91,6 +94,7 @@ struct Ctrl {
     int pad;
     long long last;     // last phase in which this block lowered a point, -1 if none
     unsigned long long nlow;
+    unsigned long long ntest;
     long long peer_last[8];  // every block's `last`, pushed by the blocks themselves each phase
 };
 
@@ -167,26 +171,31 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
         if (job >= P.njobs) break;
         const ResJob J = P.jobs[job];
         const int es = J.dtype == THIN_U16 ? 2 : 1;
-        const int R = J.rows, RP = J.rp, CW = J.cw, WPR = J.wpr;
-        const int CR = R / 2;
-        const int slot_words = CR * WPR;
-        uint32_t *bits = reinterpret_cast<uint32_t *>(smem + res_bits_off(R, RP));
-        uint16_t *queue = reinterpret_cast<uint16_t *>(smem + res_queue_off(R, RP, WPR));
-        const int row0 = rank * R;
-        const int nrows = max(0, min(R, J.h - row0));
+        const int R = J.rows, HR = J.hr, RP = J.rp, CW = J.cw, WPR = J.wpr;
+        const int LR = R + 2 * HR;   // shared rows: HR halo rows, R own rows, HR halo rows
+        const int CRT = LR / 2;      // cell rows held
+        const int HC = HR / 2;       // halo cell rows on each side
+        const int slot_words = CRT * WPR;
+        uint32_t *bits = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
+        uint32_t *rec = reinterpret_cast<uint32_t *>(smem + res_rec_off(LR, RP, WPR)) + WPR;  // cell rows -1 .. CRT
+        uint16_t *queue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR));
+        const int row0 = rank * R;       // first own image row
+        const int ybase = row0 - HR;     // image row of shared row 0
         const int rowb = J.w * es;
         const char *gimg = reinterpret_cast<const char *>(J.img);
 
-        // ---- stage this block's rows
-        if (J.bulk && nrows > 0) {
+        // ---- stage own and halo rows that exist in the image
+        const int ya = max(0, ybase), yb = min(J.h, ybase + LR);
+        const int nload = max(0, yb - ya);
+        if (J.bulk && nload > 0) {
             if (tid == 0)
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                             "r"(uint32_t(nrows * rowb))
+                             "r"(uint32_t(nload * rowb))
                              : "memory");
             __syncthreads();
-            for (int r = tid; r < nrows; r += blockDim.x) {
-                const uint32_t dst = res_smem_u32(rows_base + size_t(r) * RP + 16);
-                const char *src = gimg + size_t(row0 + r) * J.pitch;
+            for (int r = tid; r < nload; r += blockDim.x) {
+                const uint32_t dst = res_smem_u32(rows_base + size_t(ya - ybase + r) * RP + 16);
+                const char *src = gimg + size_t(ya + r) * J.pitch;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                     "l"(src), "r"(uint32_t(rowb)), "r"(bar)
@@ -198,169 +207,194 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
             }
             bar_parity ^= 1u;
         } else {
-            for (int e = tid; e < nrows * rowb; e += blockDim.x) {
+            for (int e = tid; e < nload * rowb; e += blockDim.x) {
                 const int r = e / rowb, c = e - r * rowb;
-                rows_base[size_t(r) * RP + 16 + c] = uint8_t(gimg[size_t(row0 + r) * J.pitch + c]);
+                rows_base[size_t(ya - ybase + r) * RP + 16 + c] = uint8_t(gimg[size_t(ya + r) * J.pitch + c]);
             }
         }
         for (int i = tid; i < 4 * slot_words; i += blockDim.x) bits[i] = 0u;
+        if (tid < WPR) {
+            rec[-WPR + tid] = 0u;        // the cell rows just outside the held ones never count
+            rec[slot_words + tid] = 0u;
+        }
         if (tid == 0) {
             ctrl->qn[0] = 0;
             ctrl->qn[1] = 0;
             ctrl->last = -1;
             ctrl->nlow = 0;
+            ctrl->ntest = 0;
         }
         if (tid < 8) ctrl->peer_last[tid] = -1;
-        cluster.sync();  // every block's rows are in place before anyone reads a neighbour's
+        __syncthreads();
 
-        const uint8_t *rows_up = rank > 0 ? cluster.map_shared_rank(rows_base, rank - 1) : nullptr;
-        const uint8_t *rows_down = rank + 1 < C ? cluster.map_shared_rank(rows_base, rank + 1) : nullptr;
-        const uint32_t *bits_up = rank > 0 ? cluster.map_shared_rank(bits, rank - 1) : nullptr;
-        const uint32_t *bits_down = rank + 1 < C ? cluster.map_shared_rank(bits, rank + 1) : nullptr;
-        uint32_t *rec = reinterpret_cast<uint32_t *>(smem + res_rec_off(R, RP, WPR)) + WPR;  // rows -1 .. CR
+        const Ctrl *up_ctrl = rank > 0 ? cluster.map_shared_rank(ctrl, rank - 1) : nullptr;
+        (void)up_ctrl;
         const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
         const uint32_t Mcw = CW > 1 ? 0xffffffffu / uint32_t(CW) + 1u : 0u;
         const uint32_t *comp = tabs + 256;
 
         long long g = P.start_phase;
         int converged = 0;
-        int nlow = 0;
-        for (;;) {
-            const long long rel = g - P.start_phase;
-            if (P.max_phases >= 0 && rel >= P.max_phases) break;
-            const int p = int(g & 3), px = p & 1, py = p >> 1;
-            const int cur = p;  // bitmap slot of this phase's changes
-            const int s1 = int((g - 1) & 3) * slot_words, s2 = int((g - 2) & 3) * slot_words,
-                      s3 = int((g - 3) & 3) * slot_words;
-            const int qi = int(g & 1);
-            // 1a. cells that changed in phases g-3 .. g-1, one cell row beyond each edge
-            if (rel > 3) {
-                for (int wi = tid; wi < slot_words + 2 * WPR; wi += blockDim.x) {
-                    const int w2 = wi - WPR;  // word index relative to this block's first cell row
-                    uint32_t v = 0;
-                    if (w2 < 0) {
-                        if (bits_up) v = bits_up[s1 + slot_words + w2] | bits_up[s2 + slot_words + w2] | bits_up[s3 + slot_words + w2];
-                    } else if (w2 >= slot_words) {
-                        if (bits_down) v = bits_down[s1 + w2 - slot_words] | bits_down[s2 + w2 - slot_words] | bits_down[s3 + w2 - slot_words];
-                    } else {
-                        v = bits[s1 + w2] | bits[s2 + w2] | bits[s3 + w2];
-                    }
-                    rec[w2] = v;
+        int nlow = 0, ntest = 0;
+        for (;;) {  // steps of H phases between exchanges of halo rows
+            const long long done = g - P.start_phase;
+            if (P.max_phases >= 0 && done >= P.max_phases) break;
+            const int Hs = (P.max_phases >= 0 && P.max_phases - done < J.steph) ? int(P.max_phases - done) : J.steph;
+            for (int j = 0; j < Hs; ++j, ++g) {
+                const long long rel = g - P.start_phase;
+                const int p = int(g & 3), px = p & 1, py = p >> 1;
+                const int cur = p * slot_words;  // bitmap slot of this phase's changes
+                const int s1 = int((g - 1) & 3) * slot_words, s2 = int((g - 2) & 3) * slot_words,
+                          s3 = int((g - 3) & 3) * slot_words;
+                const int qi = int(g & 1);
+                // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
+                const int rr = C > 1 ? Hs - 1 - j : 0;
+                const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
+                // 1a. cells that changed in phases g-3 .. g-1
+                if (rel > 3) {
+                    for (int wi = tid; wi < slot_words; wi += blockDim.x) rec[wi] = bits[s1 + wi] | bits[s2 + wi] | bits[s3 + wi];
+                    __syncthreads();
                 }
-                __syncthreads();
-            }
-            // 1b. dirty cells of this phase (3 x 3 dilation) -> queue
-            for (int wb = warp * 32; wb < slot_words; wb += blockDim.x) {
-                const int wi = wb + lane;
-                uint32_t d = 0;
-                if (wi < slot_words) {
-                    const int cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
-                    const int i = wi - cr * WPR;
-                    const int y = row0 + 2 * cr + py;
-                    if (y >= 1 && y <= J.h - 2) {
-                        const int valid = CW - 32 * i;
-                        const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
-                        if (rel <= 3) {
-                            d = vmask;
-                        } else {
-                            const uint32_t *rp0 = rec + cr * WPR + i;
-                            const uint32_t a1 = rp0[-WPR] | rp0[0] | rp0[WPR];
-                            const uint32_t a0 = i > 0 ? rp0[-WPR - 1] | rp0[-1] | rp0[WPR - 1] : 0u;
-                            const uint32_t a2 = i + 1 < WPR ? rp0[-WPR + 1] | rp0[1] | rp0[WPR + 1] : 0u;
-                            d = (a1 | (a1 << 1) | (a0 >> 31) | (a1 >> 1) | (a2 << 31)) & vmask;
+                // 1b. dirty cells of this phase (3 x 3 dilation) -> queue
+                for (int wb = warp * 32; wb < slot_words; wb += blockDim.x) {
+                    const int wi = wb + lane;
+                    uint32_t d = 0;
+                    int cr = 0, i = 0;
+                    if (wi < slot_words) {
+                        cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
+                        i = wi - cr * WPR;
+                        const int y = ybase + 2 * cr + py;
+                        if (y >= ylo && y <= yhi) {
+                            const int valid = CW - 32 * i;
+                            const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+                            if (rel <= 3) {
+                                d = vmask;
+                            } else {
+                                const uint32_t *rp0 = rec + wi;
+                                const uint32_t a1 = rp0[-WPR] | rp0[0] | rp0[WPR];
+                                const uint32_t a0 = i > 0 ? rp0[-WPR - 1] | rp0[-1] | rp0[WPR - 1] : 0u;
+                                const uint32_t a2 = i + 1 < WPR ? rp0[-WPR + 1] | rp0[1] | rp0[WPR + 1] : 0u;
+                                d = (a1 | (a1 << 1) | (a0 >> 31) | (a1 >> 1) | (a2 << 31)) & vmask;
+                            }
                         }
+                        bits[cur + wi] = 0u;  // this slot held phase g-4
                     }
-                    bits[cur * slot_words + wi] = 0u;  // this slot held phase g-4
-                }
-                const int cnt = __popc(d);
-                int incl = cnt;
+                    const int cnt = __popc(d);
+                    int incl = cnt;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                int base = 0;
-                if (lane == 31 && total) base = atomicAdd(&ctrl->qn[qi], total);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                int pos = base + incl - cnt;
-                if (d) {
-                    const int cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
-                    const int i = wi - cr * WPR;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    int base = 0;
+                    if (lane == 31 && total) base = atomicAdd(&ctrl->qn[qi], total);
+                    base = __shfl_sync(0xffffffffu, base, 31);
+                    int pos = base + incl - cnt;
                     while (d) {
                         const int b = __ffs(d) - 1;
                         d &= d - 1;
                         queue[pos++] = uint16_t(cr * CW + 32 * i + b);
                     }
                 }
-            }
-            if (tid == 0) ctrl->qn[qi ^ 1] = 0;  // the next phase's counter
-            __syncthreads();
-            const int qn = ctrl->qn[qi];
-            // 2. test and lower the queued groups
-            bool moved_any = false;
-            for (int k = tid; k < qn; k += blockDim.x) {
-                const int code = queue[k];
-                const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
-                const int cc = code - cr * CW;
-                const int lr = 2 * cr + py;
-                uint32_t vm = 0;
+                if (tid == 0) ctrl->qn[qi ^ 1] = 0;  // the next phase's counter
+                __syncthreads();
+                const int qn = ctrl->qn[qi];
+                // 2. test and lower the queued groups; all three rows are held here
+                bool moved_own = false;
+                for (int k = tid; k < qn; k += blockDim.x) {
+                    const int code = queue[k];
+                    const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
+                    const int cc = code - cr * CW;
+                    const int lr = 2 * cr + py;
+                    const int y = ybase + lr;
+                    uint32_t vm = 0;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int x = 8 * cc + px + 2 * kk;
-                    vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int x = 8 * cc + px + 2 * kk;
+                        vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
+                    }
+                    const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
+                    ntest += __popc(in);
+                    uint8_t *rb = rows_base + size_t(lr) * RP + 16 + size_t(8 * es) * cc;
+                    uint32_t moved;
+                    if (es == 1)
+                        moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
+                    else
+                        moved = item_u16(reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
+                                         reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule,
+                                         nlow);
+                    if (moved) {
+                        atomicOr(&bits[cur + cr * WPR + (cc >> 5)], 1u << (cc & 31));
+                        if (moved & in) moved_own = true;
+                    }
                 }
-                const size_t off = 16 + size_t(8 * es) * cc;
-                uint8_t *rb = rows_base + size_t(lr) * RP + off;
-                const uint8_t *ra = lr > 0 ? rb - RP : rows_up + size_t(R - 1) * RP + off;
-                const uint8_t *rc = lr + 1 < R ? rb + RP : rows_down + off;
-                uint32_t moved;
-                if (es == 1)
-                    moved = item_u8(ra, rb, rc, px, vm, vm, comp, J.lam, P.rule, nlow);
-                else
-                    moved = item_u16(reinterpret_cast<const uint16_t *>(ra), reinterpret_cast<uint16_t *>(rb),
-                                     reinterpret_cast<const uint16_t *>(rc), px, vm, vm, tabs, J.lam, P.rule, nlow);
-                if (moved) {
-                    atomicOr(&bits[cur * slot_words + cr * WPR + (cc >> 5)], 1u << (cc & 31));
-                    moved_any = true;
-                }
+                if (__syncthreads_or(moved_own) && tid == 0) ctrl->last = g;
             }
-            if (__syncthreads_or(moved_any) && tid == 0) ctrl->last = g;
+            // ---- end of a step: every block's last change, then the stop test
             __syncthreads();
             if (tid < C) cluster.map_shared_rank(ctrl, tid)->peer_last[rank] = ctrl->last;  // push to every block
-            cluster.sync();  // phase g done everywhere
+            cluster.sync();
             long long lc = -1;
             for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
-            ++g;
-            if (g - P.start_phase >= 4 && lc < g - 3) {  // three quiet phases: fixed point
+            if (g - P.start_phase >= 4 && lc < g - 3) {  // three quiet phases everywhere: fixed point
                 converged = 1;
                 break;
+            }
+            if (P.max_phases >= 0 && g - P.start_phase >= P.max_phases) break;
+            if (C > 1) {
+                // halo rows and their change bitmaps from the blocks above and below (their own rows)
+                const int vrow = RP / 16;
+                if (rank > 0) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank - 1) + size_t(R) * RP);
+                    uint4 *dst = reinterpret_cast<uint4 *>(rows_base);
+                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
+                    const uint32_t *bsrc = cluster.map_shared_rank(bits, rank - 1);
+                    for (int e = tid; e < 4 * HC * WPR; e += blockDim.x) {
+                        const int sl = e / (HC * WPR), o = e - sl * HC * WPR;
+                        bits[sl * slot_words + o] = bsrc[sl * slot_words + (R / 2) * WPR + o];
+                    }
+                }
+                if (rank + 1 < C) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank + 1) + size_t(HR) * RP);
+                    uint4 *dst = reinterpret_cast<uint4 *>(rows_base + size_t(HR + R) * RP);
+                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
+                    const uint32_t *bsrc = cluster.map_shared_rank(bits, rank + 1);
+                    for (int e = tid; e < 4 * HC * WPR; e += blockDim.x) {
+                        const int sl = e / (HC * WPR), o = e - sl * HC * WPR;
+                        bits[sl * slot_words + (HC + R / 2) * WPR + o] = bsrc[sl * slot_words + HC * WPR + o];
+                    }
+                }
+                cluster.sync();  // nobody changes its own rows before its neighbours have copied them
             }
         }
         // ---- results
         nlow = __reduce_add_sync(0xffffffffu, nlow);
+        ntest = __reduce_add_sync(0xffffffffu, ntest);
         if (lane == 0 && nlow) atomicAdd(&ctrl->nlow, (unsigned long long)nlow);
+        if (lane == 0 && ntest) atomicAdd(&ctrl->ntest, (unsigned long long)ntest);
         __syncthreads();
         {
-            const int ra = max(row0, 1), rb = min(row0 + nrows, J.h - 1);  // border rows never change
+            const int ra = max(row0, 1), rb = min(row0 + R, J.h - 1);  // border rows never change
             char *gout = reinterpret_cast<char *>(J.img);
             if (J.bulk) {
                 const int vpr = rowb / 16;
-                for (int e = tid; e < (rb - ra) * vpr; e += blockDim.x) {
+                for (int e = tid; e < max(0, rb - ra) * vpr; e += blockDim.x) {
                     const int r = e / vpr, c = e - r * vpr;
                     *reinterpret_cast<uint4 *>(gout + size_t(ra + r) * J.pitch + 16 * c) =
-                        *reinterpret_cast<const uint4 *>(rows_base + size_t(ra + r - row0) * RP + 16 + 16 * c);
+                        *reinterpret_cast<const uint4 *>(rows_base + size_t(ra + r - ybase) * RP + 16 + 16 * c);
                 }
             } else {
-                for (int e = tid; e < (rb - ra) * rowb; e += blockDim.x) {
+                for (int e = tid; e < max(0, rb - ra) * rowb; e += blockDim.x) {
                     const int r = e / rowb, c = e - r * rowb;
-                    gout[size_t(ra + r) * J.pitch + c] = char(rows_base[size_t(ra + r - row0) * RP + 16 + c]);
+                    gout[size_t(ra + r) * J.pitch + c] = char(rows_base[size_t(ra + r - ybase) * RP + 16 + c]);
                 }
             }
         }
         if (tid == 0) {
             ResStat &S = P.st[job];
             atomicAdd(&S.lowered, ctrl->nlow);
+            atomicAdd(&S.tested, ctrl->ntest);
             if (rank == 0) {
                 long long lc = -1;
                 for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
@@ -385,8 +419,9 @@ int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_
     for (int C = 1; C <= 8; C *= 2) {
         int rows = (h + C - 1) / C;
         rows += rows & 1;
-        if (rows / 2 * cw > 65535) continue;  // queue codes are 16-bit
-        if (res_smem_bytes(rows, rp, cw, wpr) <= smem_limit) {
+        const int held = rows + (C > 1 ? 2 * std::min(kResStep, rows) : 0);  // halo: see resident_run
+        if (held / 2 * cw > 65535) continue;  // queue codes are 16-bit
+        if (res_smem_bytes(held, rp, cw, wpr) <= smem_limit) {
             if (rows_out) *rows_out = rows;
             if (rp_out) *rp_out = rp;
             return C;
@@ -434,13 +469,17 @@ int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cud
         int rows = (J.h + C - 1) / C;
         rows += rows & 1;
         r.rows = rows;
+        // halo rows must be own rows of the neighbouring block: never deeper than a block's share
+        r.steph = std::min(kResStep, rows);
+        r.hr = C > 1 ? r.steph : 0;
         r.rp = int((size_t(J.w) * es + 15) / 16 * 16) + 32;
         r.cw = (J.w + 7) / 8;
         r.wpr = (r.cw + 31) / 32;
         r.bulk = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0) && ((size_t(J.w) * es) % 16 == 0);
         r.index = k;
-        const size_t need = res_smem_bytes(r.rows, r.rp, r.cw, r.wpr);
-        if (need > limit || r.rows / 2 * r.cw > 65535) return THIN_ERR_ARG;
+        const int held = r.rows + 2 * r.hr;
+        const size_t need = res_smem_bytes(held, r.rp, r.cw, r.wpr);
+        if (need > limit || held / 2 * r.cw > 65535) return THIN_ERR_ARG;
         smem = std::max(smem, need);
     }
     // longest-first: larger lambda and larger images tend to run longer
@@ -529,6 +568,7 @@ int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cud
                 o.end_phase = opt.start_phase + S.phases;
                 o.tiles_visited = 0;
                 o.steps = S.phases;
+                o.tested = (int64_t)S.tested;
                 if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
             }
         }

@@ -66,6 +66,7 @@ struct ImgDesc {
 struct ImgStat {
     unsigned long long lowered;
     unsigned long long tiles_visited;
+    unsigned long long tested;  // point tests on tile interiors
     long long last_change;  // global phase index, -1 if none
     int last_step;          // last step that visited a tile of this image
     int last_listed;        // last step for which a tile of this image was listed
@@ -248,7 +249,7 @@ struct Visit {
 // image border; after Hs phases the tile interior is exact.
 template <typename T>
 __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_t *queue, const Visit &V,
-                             const uint32_t *tabs, int &nlow, int &chg_j)
+                             const uint32_t *tabs, int &nlow, int &chg_j, int &ntest)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt_lanes = (1u << lane) - 1u;
@@ -301,6 +302,7 @@ __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_
                 vm |= (unsigned(sb + px + 2 * kk - slo) <= unsigned(shi - slo) ? 1u : 0u) << (8 * kk);
             const bool inside = unsigned(sr - V.hr) < unsigned(V.th) && sb >= V.pad && sb < V.pad + V.tw;
             const uint32_t in = inside ? vm : 0u;
+            ntest += __popc(in);
             uint32_t moved;
             T *rb = tile + sr * bw + sb;
             if (sizeof(T) == 1)
@@ -456,12 +458,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
                 break;
             }
             __syncwarp();
-            int nlow = 0, chg_j = -1;
+            int nlow = 0, chg_j = -1, ntest = 0;
             if (u16)
                 visit_phases<uint16_t>(reinterpret_cast<uint16_t *>(tile), bw, cells, WL.ccols, queue, V, tabs, nlow,
-                                       chg_j);
+                                       chg_j, ntest);
             else
-                visit_phases<uint8_t>(tile, bw, cells, WL.ccols, queue, V, tabs, nlow, chg_j);
+                visit_phases<uint8_t>(tile, bw, cells, WL.ccols, queue, V, tabs, nlow, chg_j, ntest);
             tile_store(tile, bw * es, es, V, dst, pitch);
             // stamps of the interior cells back to the image's stamp grid
             {
@@ -479,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
                 }
             }
             nlow = __reduce_add_sync(0xffffffffu, nlow);
+            ntest = __reduce_add_sync(0xffffffffu, ntest);
             const int maxj = __reduce_max_sync(0xffffffffu, chg_j);
             // order this warp's generic shared and global writes before later TMA traffic
             asm volatile("fence.proxy.async;" ::: "memory");
@@ -501,6 +504,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
                 if (nlow) atomicAdd(&P.st[img].lowered, (unsigned long long)nlow);
                 if (maxj >= 0) atomicMax(&P.st[img].last_change, g0 + maxj);
                 atomicAdd(&P.st[img].tiles_visited, 1ull);
+                atomicAdd(&P.st[img].tested, (unsigned long long)ntest);
                 atomicMax(&P.st[img].last_step, s);
             }
             __syncwarp();
@@ -716,6 +720,7 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
     for (auto &s : st0) {
         s.lowered = 0;
         s.tiles_visited = 0;
+        s.tested = 0;
         s.last_change = -1;
         s.last_step = -1;
         s.last_listed = 0;
@@ -787,6 +792,7 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
                 o.last_change_phase = S.last_change;
                 o.end_phase = opt.start_phase + phases;
                 o.tiles_visited = (int64_t)S.tiles_visited;
+                o.tested = (int64_t)S.tested;
                 o.steps = steps;
                 if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
             }
@@ -938,6 +944,7 @@ int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t st
     ImgStat st0;
     st0.lowered = 0;
     st0.tiles_visited = 0;
+    st0.tested = 0;
     st0.last_change = -1;
     st0.last_step = -1;
     st0.last_listed = 0;
@@ -1006,6 +1013,7 @@ int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t st
             out->last_change_phase = S.last_change;
             out->end_phase = opt.start_phase + phases;
             out->tiles_visited = (int64_t)S.tiles_visited;
+            out->tested = (int64_t)S.tested;
             out->steps = steps;
             rc = out->status;
         }

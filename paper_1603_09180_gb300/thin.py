@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("converged", ctypes.c_int32), ("phases", ctypes.c_int64),
                 ("lowered", ctypes.c_int64), ("last_change_phase", ctypes.c_int64), ("end_phase", ctypes.c_int64),
-                ("tiles_visited", ctypes.c_int64), ("steps", ctypes.c_int64)]
+                ("tiles_visited", ctypes.c_int64), ("steps", ctypes.c_int64), ("tested", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

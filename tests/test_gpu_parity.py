@@ -176,9 +176,11 @@ def test_config1_full_size(kernel):
 
 
 @pytest.mark.parametrize("shape,dt,lam", [((200, 300), "u8", 9), ((512, 512), "u8", 5), ((700, 700), "u8", 0),
-                                          ((1024, 1024), "u8", 0), ((512, 512), "u16", 0), ((333, 250), "u16", 7)])
+                                          ((1024, 1024), "u8", 0), ((512, 512), "u16", 0), ((333, 250), "u16", 7),
+                                          ((12, 20000), "u8", 5)])  # 8 blocks of 2 own rows: halo of 2
 def test_resident_cluster_sizes(shape, dt, lam):
-    """Images that need 1, 2, 4 and 8 blocks per cluster, alone and in a batch."""
+    """Images that need 1, 2, 4 and 8 blocks per cluster, alone and in a batch (a single
+    image is spread over a wider cluster, down to 32 rows per block)."""
     img = synth.value_noise_image(*shape, dt, seed=shape[0] + shape[1])
     check(img, lam, kernel="resident")
     ref, rst = oracle.thin(img, lam)
@@ -201,3 +203,14 @@ def test_timeout_reports_status_and_context_survives(monkeypatch):
     assert st["rc"] == thin.THIN_ERR_TIMEOUT and st["status"] == thin.THIN_ERR_TIMEOUT
     monkeypatch.delenv("THIN_TIMEOUT_NS")
     check(img, 0, kernel="tiled")
+
+
+def test_tested_counts():
+    """The naive engine tests every interior point of the phase's parity; the
+    others test a subset, never more."""
+    img = synth.value_noise_image(130, 170, "u8", seed=41)
+    st_n, rst = check(img, 6, kernel="naive")
+    assert st_n["tested"] == st_n["phases"] * 128 * 168 // 4
+    for kernel in ("tiled", "resident"):
+        st, _ = check(img, 6, kernel=kernel)
+        assert 0 < st["tested"] <= st_n["tested"] + 4 * 128 * 168  # the last quiet phases may run past
