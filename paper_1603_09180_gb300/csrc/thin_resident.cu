@@ -91,7 +91,7 @@ constexpr int kOffRows = 2304;   // image rows (16-byte aligned)
 struct Ctrl {
     int job;
     int qn[2];          // queue length, double-buffered by phase parity
-    int pad;
+    int lqn;            // groups that lower in this phase
     long long last;     // last phase in which this block lowered a point, -1 if none
     unsigned long long nlow;
     unsigned long long ntest;
@@ -99,18 +99,19 @@ struct Ctrl {
 };
 
 __host__ __device__ inline size_t res_bits_off(int rows, int rp) { return (kOffRows + size_t(rows) * rp + 15) / 16 * 16; }
-// four change bitmaps, then the OR of the last three with one cell row above and below
-__host__ __device__ inline size_t res_rec_off(int rows, int rp, int wpr)
+// four dirty bitmaps (one per parity), then the phase's queue of groups
+__host__ __device__ inline size_t res_queue_off(int rows, int rp, int wpr)
 {
     return res_bits_off(rows, rp) + size_t(4) * 4 * (rows / 2) * wpr;
 }
-__host__ __device__ inline size_t res_queue_off(int rows, int rp, int wpr)
+// second queue: the groups of a phase that will be lowered
+__host__ __device__ inline size_t res_lqueue_off(int rows, int rp, int cw, int wpr)
 {
-    return res_rec_off(rows, rp, wpr) + size_t(4) * (rows / 2 + 2) * wpr;
+    return res_queue_off(rows, rp, wpr) + (size_t(2) * (rows / 2) * cw + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t res_smem_bytes(int rows, int rp, int cw, int wpr)
 {
-    return res_queue_off(rows, rp, wpr) + size_t(2) * (rows / 2) * cw + 16;
+    return res_lqueue_off(rows, rp, cw, wpr) + size_t(2) * (rows / 2) * cw + 16;
 }
 
 __device__ __forceinline__ unsigned long long res_gtimer()
@@ -138,6 +139,28 @@ __device__ bool res_mbar_wait(uint32_t bar, uint32_t parity, unsigned long long 
         if (ok) return true;
         if (res_gtimer() - t0 > timeout_ns) return false;
     }
+}
+
+// Marks, in the dirty bitmap `bm` of one parity, the group in cell row cr,
+// column cc, and the groups left (lo) and right (hi) of it.
+__device__ __forceinline__ void mark_groups(uint32_t *bm, int wpr, int cr, int cc, bool lo, bool hi)
+{
+    uint32_t *row = bm + cr * wpr;
+    const int w = cc >> 5, b = cc & 31;
+    uint32_t m = 1u << b;
+    if (lo) {
+        if (b > 0)
+            m |= 1u << (b - 1);
+        else
+            atomicOr(&row[w - 1], 0x80000000u);
+    }
+    if (hi) {
+        if (b < 31)
+            m |= 1u << (b + 1);
+        else
+            atomicOr(&row[w + 1], 1u);
+    }
+    atomicOr(&row[w], m);
 }
 
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
@@ -176,9 +199,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
         const int CRT = LR / 2;      // cell rows held
         const int HC = HR / 2;       // halo cell rows on each side
         const int slot_words = CRT * WPR;
-        uint32_t *bits = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
-        uint32_t *rec = reinterpret_cast<uint32_t *>(smem + res_rec_off(LR, RP, WPR)) + WPR;  // cell rows -1 .. CRT
+        // dirty[q]: per parity q = 2 (y & 1) + (x & 1), one bit per 4-point group (cell row, column):
+        // some neighbour of a point of the group moved since the group's last test
+        uint32_t *dirty = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
         uint16_t *queue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR));
+        uint16_t *lqueue = reinterpret_cast<uint16_t *>(smem + res_lqueue_off(LR, RP, CW, WPR));
         const int row0 = rank * R;       // first own image row
         const int ybase = row0 - HR;     // image row of shared row 0
         const int rowb = J.w * es;
@@ -212,14 +237,12 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                 rows_base[size_t(ya - ybase + r) * RP + 16 + c] = uint8_t(gimg[size_t(ya + r) * J.pitch + c]);
             }
         }
-        for (int i = tid; i < 4 * slot_words; i += blockDim.x) bits[i] = 0u;
-        if (tid < WPR) {
-            rec[-WPR + tid] = 0u;        // the cell rows just outside the held ones never count
-            rec[slot_words + tid] = 0u;
-        }
+        // every group is tested in the first phase of its parity
+        for (int i = tid; i < 4 * slot_words; i += blockDim.x) dirty[i] = 0xffffffffu;
         if (tid == 0) {
             ctrl->qn[0] = 0;
             ctrl->qn[1] = 0;
+            ctrl->lqn = 0;
             ctrl->last = -1;
             ctrl->nlow = 0;
             ctrl->ntest = 0;
@@ -227,8 +250,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
         if (tid < 8) ctrl->peer_last[tid] = -1;
         __syncthreads();
 
-        const Ctrl *up_ctrl = rank > 0 ? cluster.map_shared_rank(ctrl, rank - 1) : nullptr;
-        (void)up_ctrl;
         const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
         const uint32_t Mcw = CW > 1 ? 0xffffffffu / uint32_t(CW) + 1u : 0u;
         const uint32_t *comp = tabs + 256;
@@ -241,21 +262,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
             if (P.max_phases >= 0 && done >= P.max_phases) break;
             const int Hs = (P.max_phases >= 0 && P.max_phases - done < J.steph) ? int(P.max_phases - done) : J.steph;
             for (int j = 0; j < Hs; ++j, ++g) {
-                const long long rel = g - P.start_phase;
                 const int p = int(g & 3), px = p & 1, py = p >> 1;
-                const int cur = p * slot_words;  // bitmap slot of this phase's changes
-                const int s1 = int((g - 1) & 3) * slot_words, s2 = int((g - 2) & 3) * slot_words,
-                          s3 = int((g - 3) & 3) * slot_words;
+                uint32_t *dp = dirty + p * slot_words;
+                uint32_t *d_row = dirty + (2 * py + (px ^ 1)) * slot_words;   // same rows, other columns
+                uint32_t *d_col = dirty + (2 * (py ^ 1) + px) * slot_words;   // rows above and below
+                uint32_t *d_diag = dirty + (2 * (py ^ 1) + (px ^ 1)) * slot_words;
                 const int qi = int(g & 1);
                 // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
                 const int rr = C > 1 ? Hs - 1 - j : 0;
                 const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
-                // 1a. cells that changed in phases g-3 .. g-1
-                if (rel > 3) {
-                    for (int wi = tid; wi < slot_words; wi += blockDim.x) rec[wi] = bits[s1 + wi] | bits[s2 + wi] | bits[s3 + wi];
-                    __syncthreads();
-                }
-                // 1b. dirty cells of this phase (3 x 3 dilation) -> queue
+                // 1. this parity's dirty groups -> queue (the bits are consumed)
                 for (int wb = warp * 32; wb < slot_words; wb += blockDim.x) {
                     const int wi = wb + lane;
                     uint32_t d = 0;
@@ -266,18 +282,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                         const int y = ybase + 2 * cr + py;
                         if (y >= ylo && y <= yhi) {
                             const int valid = CW - 32 * i;
-                            const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
-                            if (rel <= 3) {
-                                d = vmask;
-                            } else {
-                                const uint32_t *rp0 = rec + wi;
-                                const uint32_t a1 = rp0[-WPR] | rp0[0] | rp0[WPR];
-                                const uint32_t a0 = i > 0 ? rp0[-WPR - 1] | rp0[-1] | rp0[WPR - 1] : 0u;
-                                const uint32_t a2 = i + 1 < WPR ? rp0[-WPR + 1] | rp0[1] | rp0[WPR + 1] : 0u;
-                                d = (a1 | (a1 << 1) | (a0 >> 31) | (a1 >> 1) | (a2 << 31)) & vmask;
-                            }
+                            d = dp[wi] & (valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u));
                         }
-                        bits[cur + wi] = 0u;  // this slot held phase g-4
+                        dp[wi] = 0u;
                     }
                     const int cnt = __popc(d);
                     int incl = cnt;
@@ -300,10 +307,70 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                 if (tid == 0) ctrl->qn[qi ^ 1] = 0;  // the next phase's counter
                 __syncthreads();
                 const int qn = ctrl->qn[qi];
-                // 2. test and lower the queued groups; all three rows are held here
+                // the groups of the other three parities next to a moved point become dirty
+                auto mark = [&](int cr, int cc, int px_, int py_, uint32_t moved) {
+                    const bool lo = px_ == 0 && (moved & 1u);           // x - 1 of point 0 is left of the block
+                    const bool hi = px_ == 1 && (moved & 0x01000000u);  // x + 1 of point 3 is right of it
+                    mark_groups(d_row, WPR, cr, cc, lo, hi);
+                    const int ca = cr - 1 + py_, cb = cr + py_;          // cell rows of rows y - 1, y + 1
+                    if (ca >= 0) {
+                        mark_groups(d_col, WPR, ca, cc, false, false);
+                        mark_groups(d_diag, WPR, ca, cc, lo, hi);
+                    }
+                    if (cb < CRT) {
+                        mark_groups(d_col, WPR, cb, cc, false, false);
+                        mark_groups(d_diag, WPR, cb, cc, lo, hi);
+                    }
+                };
+                // 2a. test every queued group once; the few that lower go to a second queue, so
+                // that the lowering loop below runs on densely packed lanes (u16 groups are
+                // lowered right here, one point at a time)
                 bool moved_own = false;
-                for (int k = tid; k < qn; k += blockDim.x) {
-                    const int code = queue[k];
+                for (int kb = warp * 32; kb < qn; kb += blockDim.x) {
+                    const int k = kb + lane;
+                    bool lowers = false;
+                    int code = 0;
+                    if (k < qn) {
+                        code = queue[k];
+                        const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
+                        const int cc = code - cr * CW;
+                        const int lr = 2 * cr + py;
+                        const int y = ybase + lr;
+                        uint32_t vm = 0;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const int x = 8 * cc + px + 2 * kk;
+                            vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
+                        }
+                        const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
+                        ntest += __popc(in);
+                        uint8_t *rb = rows_base + size_t(lr) * RP + 16 + size_t(8 * es) * cc;
+                        if (es == 1) {
+                            lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, P.rule) != 0;
+                        } else {
+                            const uint32_t moved =
+                                item_u16(reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
+                                         reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule,
+                                         nlow);
+                            if (moved) {
+                                mark(cr, cc, px, py, moved);
+                                if (moved & in) moved_own = true;
+                            }
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, lowers);
+                    if (bal) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&ctrl->lqn, __popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (lowers) lqueue[base + __popc(bal & ((1u << lane) - 1u))] = uint16_t(code);
+                    }
+                }
+                __syncthreads();
+                const int lqn = ctrl->lqn;
+                // 2b. lower them
+                for (int k = tid; k < lqn; k += blockDim.x) {
+                    const int code = lqueue[k];
                     const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
                     const int cc = code - cr * CW;
                     const int lr = 2 * cr + py;
@@ -314,22 +381,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                         const int x = 8 * cc + px + 2 * kk;
                         vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
                     }
-                    const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
-                    ntest += __popc(in);
-                    uint8_t *rb = rows_base + size_t(lr) * RP + 16 + size_t(8 * es) * cc;
-                    uint32_t moved;
-                    if (es == 1)
-                        moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
-                    else
-                        moved = item_u16(reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
-                                         reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule,
-                                         nlow);
+                    const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;
+                    uint8_t *rb = rows_base + size_t(lr) * RP + 16 + cc * 8;
+                    const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
                     if (moved) {
-                        atomicOr(&bits[cur + cr * WPR + (cc >> 5)], 1u << (cc & 31));
+                        mark(cr, cc, px, py, moved);
                         if (moved & in) moved_own = true;
                     }
                 }
                 if (__syncthreads_or(moved_own) && tid == 0) ctrl->last = g;
+                if (tid == 0) ctrl->lqn = 0;  // every thread read it before the barrier above
             }
             // ---- end of a step: every block's last change, then the stop test
             __syncthreads();
@@ -343,26 +404,36 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
             }
             if (P.max_phases >= 0 && g - P.start_phase >= P.max_phases) break;
             if (C > 1) {
-                // halo rows and their change bitmaps from the blocks above and below (their own rows)
+                // halo rows and their dirty bits from the blocks above and below (their own rows);
+                // the marks a neighbour made on my first or last row (from its own rows, which I
+                // do not follow to the end of a step) are merged into mine
                 const int vrow = RP / 16;
                 if (rank > 0) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank - 1) + size_t(R) * RP);
+                    const uint8_t *nrows = cluster.map_shared_rank(rows_base, rank - 1);
+                    const uint32_t *nd = cluster.map_shared_rank(dirty, rank - 1);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(nrows + size_t(R) * RP);
                     uint4 *dst = reinterpret_cast<uint4 *>(rows_base);
                     for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
-                    const uint32_t *bsrc = cluster.map_shared_rank(bits, rank - 1);
-                    for (int e = tid; e < 4 * HC * WPR; e += blockDim.x) {
-                        const int sl = e / (HC * WPR), o = e - sl * HC * WPR;
-                        bits[sl * slot_words + o] = bsrc[sl * slot_words + (R / 2) * WPR + o];
+                    for (int e = tid; e < 4 * (HC + 1) * WPR; e += blockDim.x) {
+                        // neighbour cell rows R/2 .. R/2 + HC -> mine 0 .. HC
+                        const int q = e / ((HC + 1) * WPR), o = e - q * (HC + 1) * WPR;
+                        const uint32_t v = nd[q * slot_words + (R / 2) * WPR + o];
+                        uint32_t &d = dirty[q * slot_words + o];
+                        d = o < (HC - 1) * WPR ? v : (d | v);  // the two cell rows at the seam: both blocks' marks
                     }
                 }
                 if (rank + 1 < C) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank + 1) + size_t(HR) * RP);
+                    const uint8_t *nrows = cluster.map_shared_rank(rows_base, rank + 1);
+                    const uint32_t *nd = cluster.map_shared_rank(dirty, rank + 1);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(nrows + size_t(HR) * RP);
                     uint4 *dst = reinterpret_cast<uint4 *>(rows_base + size_t(HR + R) * RP);
                     for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
-                    const uint32_t *bsrc = cluster.map_shared_rank(bits, rank + 1);
-                    for (int e = tid; e < 4 * HC * WPR; e += blockDim.x) {
-                        const int sl = e / (HC * WPR), o = e - sl * HC * WPR;
-                        bits[sl * slot_words + (HC + R / 2) * WPR + o] = bsrc[sl * slot_words + HC * WPR + o];
+                    for (int e = tid; e < 4 * (HC + 1) * WPR; e += blockDim.x) {
+                        // neighbour cell rows HC - 1 .. 2 HC - 1 -> mine HC + R/2 - 1 .. 2 HC + R/2 - 1
+                        const int q = e / ((HC + 1) * WPR), o = e - q * (HC + 1) * WPR;
+                        const uint32_t v = nd[q * slot_words + (HC - 1) * WPR + o];
+                        uint32_t &d = dirty[q * slot_words + (HC + R / 2 - 1) * WPR + o];
+                        d = o >= 2 * WPR ? v : (d | v);
                     }
                 }
                 cluster.sync();  // nobody changes its own rows before its neighbours have copied them

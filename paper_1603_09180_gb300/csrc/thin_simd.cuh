@@ -53,58 +53,69 @@ __device__ __forceinline__ uint32_t merge_dirs(const uint32_t lt[8])
            (lt[6] >> 1) | lt[7];
 }
 
-// The lowering loop of Sec. 2.2 on four points of one parity at once (bytes
-// of `c`), neighbours fixed (bytes of nb[d], ring order E, NE, N, NW, W, SW,
-// S, SE).  For each point: Gamma^-- is its lower-neighbour mask M; T-- is the
+// Lambda-destructibility (Sec. 2.1) of four points of one parity at once
+// (bytes of `c`), neighbours nb[d] in ring order E, NE, N, NW, W, SW, S, SE.
+// For each point: Gamma^-- is its lower-neighbour mask (byte of M); T-- is the
 // number of runs of M once isolated lower corners (those with no lower
 // 4-neighbour beside them, never 4-adjacent to x) are dropped; under (8,4),
 // T+ = T-- except when no 4-neighbour is lower (T-- = 0) or all eight are
 // (T+ = 0), so "destructible" is "exactly one run start".  k-divergent points
 // (two or more runs) are lambda-destructible when at most one of their
-// counted components fails F(x) - F^-(c) <= lambda.  `vm` has 0x01 in the
-// bytes of points that may move.  Returns the bytes lowered (0x01 each) over
-// all iterations; `c` receives the new values, `nin` the lowering steps of the
-// points also in `in`.  `comp` is the component-mask table.
+// counted components fails F(x) - F^-(c) <= lambda.  Returns 0x01 in the
+// bytes of the lambda-destructible points among those set in `vm`.
+__device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
+                                            uint32_t lam, int rule, uint32_t &M)
+{
+    const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
+    uint32_t lt[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) lt[d] = lt8(nb[d], c, bl, bh);
+    M = merge_dirs(lt);
+    const uint32_t iso = M & 0xaaaaaaaau & ~rot_prev(M) & ~rot_next(M);
+    const uint32_t mc = M ^ iso;                              // counted lower neighbours
+    const uint32_t st = mc & ~rot_prev(mc);                   // starts of their runs
+    const uint32_t t = st & ((st | kMsb8) - kLsb8);           // starts minus the lowest one
+    const uint32_t nzt = nonzero8(t);
+    uint32_t ok = ((nonzero8(st) & ~nzt) >> 7) & vm;          // destructible
+    const uint32_t dv = (nzt >> 7) & vm;                      // k-divergent
+    if (lam != 0 && dv) {
+        // deep lower neighbours: value < F(x) - lambda (none when F(x) <= lambda)
+        const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
+        const uint32_t cl = __vsubus4(c, lrep);
+        const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
+        uint32_t dp[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
+        const uint32_t deep = merge_dirs(dp) & mc;
+        // F^- = max: a component fails when no member is shallow (value >= F(x) - lambda);
+        // F^- = min: a component fails when some member is deep
+        const uint32_t probe = rule == 0 ? (mc & ~deep) : deep;
+        uint32_t okdv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t e = comp[(M >> (8 * k)) & 0xffu];  // component masks, one per byte
+            const uint32_t hit = __popc(nonzero8(e & (((probe >> (8 * k)) & 0xffu) * kLsb8)));
+            const uint32_t bad = rule == 0 ? __popc(nonzero8(e)) - hit : hit;
+            okdv |= (bad <= 1 ? 1u : 0u) << (8 * k);
+        }
+        ok |= okdv & dv;
+    }
+    return ok & 0x01010101u;
+}
+
+// The lowering loop of Sec. 2.2 on the four points: while a point is
+// lambda-destructible, F(x) := alpha^-(x, F), its neighbours fixed.  Returns
+// the bytes lowered (0x01 each) over all iterations; `c` receives the new
+// values, `nin` the lowering steps of the points also in `in`.  `comp` is the
+// component-mask table.
 __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
                                            const uint32_t *comp, uint32_t lam, int rule, int &nin)
 {
     uint32_t okacc = 0;
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
-        const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
-        uint32_t lt[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) lt[d] = lt8(nb[d], c, bl, bh);
-        const uint32_t M = merge_dirs(lt);
-        const uint32_t iso = M & 0xaaaaaaaau & ~rot_prev(M) & ~rot_next(M);
-        const uint32_t mc = M ^ iso;                              // counted lower neighbours
-        const uint32_t st = mc & ~rot_prev(mc);                   // starts of their runs
-        const uint32_t t = st & ((st | kMsb8) - kLsb8);           // starts minus the lowest one
-        const uint32_t nzt = nonzero8(t);
-        uint32_t ok = ((nonzero8(st) & ~nzt) >> 7) & vm;          // destructible
-        const uint32_t dv = (nzt >> 7) & vm;                      // k-divergent
-        if (lam != 0 && dv) {
-            // deep lower neighbours: value < F(x) - lambda (none when F(x) <= lambda)
-            const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
-            const uint32_t cl = __vsubus4(c, lrep);
-            const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
-            uint32_t dp[8];
-#pragma unroll
-            for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
-            const uint32_t deep = merge_dirs(dp) & mc;
-            // F^- = max: a component fails when no member is shallow (value >= F(x) - lambda);
-            // F^- = min: a component fails when some member is deep
-            const uint32_t probe = rule == 0 ? (mc & ~deep) : deep;
-            uint32_t okdv = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t e = comp[(M >> (8 * k)) & 0xffu];  // component masks, one per byte
-                const uint32_t hit = __popc(nonzero8(e & (((probe >> (8 * k)) & 0xffu) * kLsb8)));
-                const uint32_t bad = rule == 0 ? __popc(nonzero8(e)) - hit : hit;
-                okdv |= (bad <= 1 ? 1u : 0u) << (8 * k);
-            }
-            ok |= okdv & dv;
-        }
+        uint32_t M;
+        const uint32_t ok = decide4(c, nb, vm, comp, lam, rule, M);
         if (!ok) break;
         // alpha^-: largest lower neighbour, by a tree of byte maxima; direction d
         // of point k is lower iff bit d of byte k of M is set
@@ -121,10 +132,12 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
     return okacc;
 }
 
-// One u8 work item.  ra, rb, rc point at the 8-byte aligned block in rows
-// y - 1, y, y + 1; the words at -4 and +8 of each must be readable.
-__device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
-                                            uint32_t in, const uint32_t *comp, uint32_t lam, int rule, int &nin)
+// Gathers a u8 work item: the centre bytes and the eight neighbour vectors of
+// the four points.  ra, rb, rc point at the 8-byte aligned block in rows y - 1,
+// y, y + 1; the words at -4 and +8 of each must be readable.  `other` gets the
+// bytes of row y of the other column parity (to rebuild the block).
+__device__ __forceinline__ void gather_u8(const uint8_t *ra, const uint8_t *rb, const uint8_t *rc, int px,
+                                          uint32_t nb[8], uint32_t &c, uint32_t &other)
 {
     const uint2 wa = *reinterpret_cast<const uint2 *>(ra);
     const uint2 wb = *reinterpret_cast<const uint2 *>(rb);
@@ -132,12 +145,12 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
     const uint32_t Ea = __byte_perm(wa.x, wa.y, 0x6420), Oa = __byte_perm(wa.x, wa.y, 0x7531);
     const uint32_t Eb = __byte_perm(wb.x, wb.y, 0x6420), Ob = __byte_perm(wb.x, wb.y, 0x7531);
     const uint32_t Ec = __byte_perm(wc.x, wc.y, 0x6420), Oc = __byte_perm(wc.x, wc.y, 0x7531);
-    uint32_t nb[8], c;
     if (px == 0) {
         const uint32_t La = *reinterpret_cast<const uint32_t *>(ra - 4);
         const uint32_t Lb = *reinterpret_cast<const uint32_t *>(rb - 4);
         const uint32_t Lc = *reinterpret_cast<const uint32_t *>(rc - 4);
         c = Eb;
+        other = Ob;
         nb[0] = Ob;
         nb[1] = Oa;
         nb[2] = Ea;
@@ -151,6 +164,7 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
         const uint32_t Rb = *reinterpret_cast<const uint32_t *>(rb + 8);
         const uint32_t Rc = *reinterpret_cast<const uint32_t *>(rc + 8);
         c = Ob;
+        other = Eb;
         nb[0] = __byte_perm(Eb, Rb, 0x4321);
         nb[1] = __byte_perm(Ea, Ra, 0x4321);
         nb[2] = Oa;
@@ -160,13 +174,30 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
         nb[6] = Oc;
         nb[7] = __byte_perm(Ec, Rc, 0x4321);
     }
+}
+
+// One u8 work item, tested only: 0x01 in the bytes of the points that would be lowered now.
+__device__ __forceinline__ uint32_t test_u8(const uint8_t *ra, const uint8_t *rb, const uint8_t *rc, int px,
+                                            uint32_t vm, const uint32_t *comp, uint32_t lam, int rule)
+{
+    uint32_t nb[8], c, other, M;
+    gather_u8(ra, rb, rc, px, nb, c, other);
+    return decide4(c, nb, vm, comp, lam, rule, M);
+}
+
+// One u8 work item, lowered: the lowering loop on its four points, the block written back.
+__device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
+                                            uint32_t in, const uint32_t *comp, uint32_t lam, int rule, int &nin)
+{
+    uint32_t nb[8], c, other;
+    gather_u8(ra, rb, rc, px, nb, c, other);
     const uint32_t moved = lower4(c, nb, vm, in, comp, lam, rule, nin);
     if (moved) {
         uint2 out;
         if (px == 0)
-            out = make_uint2(__byte_perm(c, Ob, 0x5140), __byte_perm(c, Ob, 0x7362));
+            out = make_uint2(__byte_perm(c, other, 0x5140), __byte_perm(c, other, 0x7362));
         else
-            out = make_uint2(__byte_perm(Eb, c, 0x5140), __byte_perm(Eb, c, 0x7362));
+            out = make_uint2(__byte_perm(other, c, 0x5140), __byte_perm(other, c, 0x7362));
         *reinterpret_cast<uint2 *>(rb) = out;
     }
     return moved;
