@@ -47,11 +47,12 @@ int check_image(const void *img, int w, int h, size_t pitch, int dt)
 int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out)
 {
     const int n = int(specs.size());
+    const int nw = 16;  // warps per resident block (one block per SM measured fastest)
     std::vector<int> cls(n, 0);
     if (o.kernel == THIN_KERNEL_AUTO || o.kernel == THIN_KERNEL_RESIDENT) {
-        const size_t limit = resident_smem_limit();
+        const size_t limit = resident_smem_limit(16 / nw);
         for (int k = 0; k < n; ++k)
-            cls[k] = resident_cluster_size(specs[k].w, specs[k].h, specs[k].dtype, limit, nullptr, nullptr);
+            cls[k] = resident_cluster_size(specs[k].w, specs[k].h, specs[k].dtype, limit, nw, nullptr, nullptr);
     }
     int eligible = 0, sms = 0, dev = 0;
     for (int k = 0; k < n; ++k) eligible += cls[k] > 0;
@@ -59,7 +60,7 @@ int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStrea
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // few images: spread each over more blocks of a wider cluster
     int spread = 1;
-    while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms) spread *= 2;
+    while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms * (16 / nw)) spread *= 2;
     int rc = THIN_OK;
     for (int C = 1; C <= 8; C *= 2) {
         std::vector<JobSpec> group;
@@ -75,7 +76,7 @@ int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStrea
         }
         if (group.empty()) continue;
         std::vector<thin_stats> st(out ? group.size() : 0);
-        const int r = resident_run(group.data(), int(group.size()), C, o, s, out ? st.data() : nullptr);
+        const int r = resident_run(group.data(), int(group.size()), C, nw, o, s, out ? st.data() : nullptr);
         if (out)
             for (size_t k = 0; k < group.size(); ++k) out[where[k]] = st[k];
         if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;

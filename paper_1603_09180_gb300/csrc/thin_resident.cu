@@ -35,7 +35,9 @@ namespace thin {
 
 namespace {
 
-constexpr int kResThreads = 1024;
+// Warps per block: 16, 8 or 4, with 1, 2 or 4 blocks per SM (at most 128
+// registers a thread either way).
+constexpr int kResMaxWarps = 16;
 constexpr int kResStep = 8;  // phases between halo exchanges = halo rows held from each neighbour
 
 struct ResJob {
@@ -90,8 +92,6 @@ constexpr int kOffRows = 2304;   // image rows (16-byte aligned)
 
 struct Ctrl {
     int job;
-    int qn[2];          // queue length, double-buffered by phase parity
-    int lqn;            // groups that lower in this phase
     long long last;     // last phase in which this block lowered a point, -1 if none
     unsigned long long nlow;
     unsigned long long ntest;
@@ -104,14 +104,18 @@ __host__ __device__ inline size_t res_queue_off(int rows, int rp, int wpr)
 {
     return res_bits_off(rows, rp) + size_t(4) * 4 * (rows / 2) * wpr;
 }
-// second queue: the groups of a phase that will be lowered
-__host__ __device__ inline size_t res_lqueue_off(int rows, int rp, int cw, int wpr)
+// In each round of 32 x nw bitmap words, warp w of nw scans the words
+// w, w + nw, w + 2 nw, ... (one per lane) and queues the groups it finds in a
+// queue of its own: at most 32 words of 32 groups.
+__host__ __device__ inline int res_warp_queue(int rows, int wpr, int nw)
 {
-    return res_queue_off(rows, rp, wpr) + (size_t(2) * (rows / 2) * cw + 15) / 16 * 16;
+    const int words = (rows / 2) * wpr;
+    const int per_warp = (words + nw - 1) / nw;
+    return (per_warp < 32 ? per_warp : 32) * 32;
 }
-__host__ __device__ inline size_t res_smem_bytes(int rows, int rp, int cw, int wpr)
+__host__ __device__ inline size_t res_smem_bytes(int rows, int rp, int wpr, int nw)
 {
-    return res_lqueue_off(rows, rp, cw, wpr) + size_t(2) * (rows / 2) * cw + 16;
+    return res_queue_off(rows, rp, wpr) + size_t(2) * nw * res_warp_queue(rows, wpr, nw) + 16;
 }
 
 __device__ __forceinline__ unsigned long long res_gtimer()
@@ -163,7 +167,8 @@ __device__ __forceinline__ void mark_groups(uint32_t *bm, int wpr, int cr, int c
     atomicOr(&row[w], m);
 }
 
-__global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -202,8 +207,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
         // dirty[q]: per parity q = 2 (y & 1) + (x & 1), one bit per 4-point group (cell row, column):
         // some neighbour of a point of the group moved since the group's last test
         uint32_t *dirty = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
-        uint16_t *queue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR));
-        uint16_t *lqueue = reinterpret_cast<uint16_t *>(smem + res_lqueue_off(LR, RP, CW, WPR));
+        const int WQ = res_warp_queue(LR, WPR, NW);
+        uint16_t *wqueue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR)) + warp * WQ;
         const int row0 = rank * R;       // first own image row
         const int ybase = row0 - HR;     // image row of shared row 0
         const int rowb = J.w * es;
@@ -240,9 +245,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
         // every group is tested in the first phase of its parity
         for (int i = tid; i < 4 * slot_words; i += blockDim.x) dirty[i] = 0xffffffffu;
         if (tid == 0) {
-            ctrl->qn[0] = 0;
-            ctrl->qn[1] = 0;
-            ctrl->lqn = 0;
             ctrl->last = -1;
             ctrl->nlow = 0;
             ctrl->ntest = 0;
@@ -267,52 +269,15 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                 uint32_t *d_row = dirty + (2 * py + (px ^ 1)) * slot_words;   // same rows, other columns
                 uint32_t *d_col = dirty + (2 * (py ^ 1) + px) * slot_words;   // rows above and below
                 uint32_t *d_diag = dirty + (2 * (py ^ 1) + (px ^ 1)) * slot_words;
-                const int qi = int(g & 1);
                 // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
                 const int rr = C > 1 ? Hs - 1 - j : 0;
                 const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
-                // 1. this parity's dirty groups -> queue (the bits are consumed)
-                for (int wb = warp * 32; wb < slot_words; wb += blockDim.x) {
-                    const int wi = wb + lane;
-                    uint32_t d = 0;
-                    int cr = 0, i = 0;
-                    if (wi < slot_words) {
-                        cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
-                        i = wi - cr * WPR;
-                        const int y = ybase + 2 * cr + py;
-                        if (y >= ylo && y <= yhi) {
-                            const int valid = CW - 32 * i;
-                            d = dp[wi] & (valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u));
-                        }
-                        dp[wi] = 0u;
-                    }
-                    const int cnt = __popc(d);
-                    int incl = cnt;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    int base = 0;
-                    if (lane == 31 && total) base = atomicAdd(&ctrl->qn[qi], total);
-                    base = __shfl_sync(0xffffffffu, base, 31);
-                    int pos = base + incl - cnt;
-                    while (d) {
-                        const int b = __ffs(d) - 1;
-                        d &= d - 1;
-                        queue[pos++] = uint16_t(cr * CW + 32 * i + b);
-                    }
-                }
-                if (tid == 0) ctrl->qn[qi ^ 1] = 0;  // the next phase's counter
-                __syncthreads();
-                const int qn = ctrl->qn[qi];
                 // the groups of the other three parities next to a moved point become dirty
-                auto mark = [&](int cr, int cc, int px_, int py_, uint32_t moved) {
-                    const bool lo = px_ == 0 && (moved & 1u);           // x - 1 of point 0 is left of the block
-                    const bool hi = px_ == 1 && (moved & 0x01000000u);  // x + 1 of point 3 is right of it
+                auto mark = [&](int cr, int cc, uint32_t moved) {
+                    const bool lo = px == 0 && (moved & 1u);           // x - 1 of point 0 is left of the block
+                    const bool hi = px == 1 && (moved & 0x01000000u);  // x + 1 of point 3 is right of it
                     mark_groups(d_row, WPR, cr, cc, lo, hi);
-                    const int ca = cr - 1 + py_, cb = cr + py_;          // cell rows of rows y - 1, y + 1
+                    const int ca = cr - 1 + py, cb = cr + py;          // cell rows of rows y - 1, y + 1
                     if (ca >= 0) {
                         mark_groups(d_col, WPR, ca, cc, false, false);
                         mark_groups(d_diag, WPR, ca, cc, lo, hi);
@@ -322,75 +287,107 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
                         mark_groups(d_diag, WPR, cb, cc, lo, hi);
                     }
                 };
-                // 2a. test every queued group once; the few that lower go to a second queue, so
-                // that the lowering loop below runs on densely packed lanes (u16 groups are
-                // lowered right here, one point at a time)
-                bool moved_own = false;
-                for (int kb = warp * 32; kb < qn; kb += blockDim.x) {
-                    const int k = kb + lane;
-                    bool lowers = false;
-                    int code = 0;
-                    if (k < qn) {
-                        code = queue[k];
-                        const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
-                        const int cc = code - cr * CW;
-                        const int lr = 2 * cr + py;
-                        const int y = ybase + lr;
-                        uint32_t vm = 0;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const int x = 8 * cc + px + 2 * kk;
-                            vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
-                        }
-                        const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
-                        ntest += __popc(in);
-                        uint8_t *rb = rows_base + size_t(lr) * RP + 16 + size_t(8 * es) * cc;
-                        if (es == 1) {
-                            lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, P.rule) != 0;
-                        } else {
-                            const uint32_t moved =
-                                item_u16(reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
-                                         reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule,
-                                         nlow);
-                            if (moved) {
-                                mark(cr, cc, px, py, moved);
-                                if (moved & in) moved_own = true;
-                            }
-                        }
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, lowers);
-                    if (bal) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&ctrl->lqn, __popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (lowers) lqueue[base + __popc(bal & ((1u << lane) - 1u))] = uint16_t(code);
-                    }
-                }
-                __syncthreads();
-                const int lqn = ctrl->lqn;
-                // 2b. lower them
-                for (int k = tid; k < lqn; k += blockDim.x) {
-                    const int code = lqueue[k];
-                    const int cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
-                    const int cc = code - cr * CW;
-                    const int lr = 2 * cr + py;
-                    const int y = ybase + lr;
-                    uint32_t vm = 0;
+                auto where = [&](int code, int &cr, int &cc, uint32_t &vm, uint32_t &in) {
+                    cr = CW > 1 ? int(__umulhi(uint32_t(code), Mcw)) : code;
+                    cc = code - cr * CW;
+                    const int y = ybase + 2 * cr + py;
+                    vm = 0;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const int x = 8 * cc + px + 2 * kk;
                         vm |= (x >= 1 && x <= J.w - 2 ? 1u : 0u) << (8 * kk);
                     }
-                    const uint32_t in = (y >= row0 && y < row0 + R) ? vm : 0u;
-                    uint8_t *rb = rows_base + size_t(lr) * RP + 16 + cc * 8;
-                    const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
-                    if (moved) {
-                        mark(cr, cc, px, py, moved);
-                        if (moved & in) moved_own = true;
+                    in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
+                };
+                bool moved_own = false;
+                // Each warp takes the bitmap words warp, warp + NW, ... of this parity,
+                // consumes their bits, and tests and lowers the groups it found on its
+                // own: no block barrier until the end of the phase.
+                for (int r0 = 0; r0 < slot_words; r0 += 32 * NW) {
+                    const int wi = r0 + lane * NW + warp;
+                    uint32_t d = 0;
+                    int cr = 0;
+                    if (wi < slot_words) {
+                        cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
+                        const int i = wi - cr * WPR;
+                        const int y = ybase + 2 * cr + py;
+                        if (y >= ylo && y <= yhi) {
+                            const int valid = CW - 32 * i;
+                            d = dp[wi] & (valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u));
+                        }
+                        if (dp[wi]) dp[wi] = 0u;
                     }
+                    const int cnt = __popc(d);
+                    int incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int nq = __shfl_sync(0xffffffffu, incl, 31);
+                    if (nq == 0) continue;
+                    {
+                        int pos = incl - cnt;
+                        const int cbase = (wi - cr * WPR) * 32 + cr * CW;
+                        while (d) {
+                            const int b = __ffs(d) - 1;
+                            d &= d - 1;
+                            wqueue[pos++] = uint16_t(cbase + b);
+                        }
+                    }
+                    __syncwarp();
+                    int nl = nq;
+                    if (es == 2 || nq > 32) {
+                        // test first; the groups that lower are packed to the front of the queue
+                        // (in place: a chunk's slots are read before any of them is written)
+                        nl = 0;
+                        for (int kb = 0; kb < nq; kb += 32) {
+                            const int k = kb + lane;
+                            bool lowers = false;
+                            int code = 0;
+                            if (k < nq) {
+                                code = wqueue[k];
+                                int gcr, gcc;
+                                uint32_t vm, in;
+                                where(code, gcr, gcc, vm, in);
+                                ntest += __popc(in);
+                                uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
+                                if (es == 1) {
+                                    lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, P.rule) != 0;
+                                } else {
+                                    const uint32_t moved = item_u16(
+                                        reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
+                                        reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule, nlow);
+                                    if (moved) {
+                                        mark(gcr, gcc, moved);
+                                        if (moved & in) moved_own = true;
+                                    }
+                                }
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, lowers);
+                            if (lowers) wqueue[nl + __popc(bal & ((1u << lane) - 1u))] = uint16_t(code);
+                            nl += __popc(bal);
+                        }
+                        __syncwarp();
+                        if (es == 2) nl = 0;
+                    }
+                    // lower them (u8); with few groups the loop's first test is the only one
+                    for (int k = lane; k < nl; k += 32) {
+                        const int code = wqueue[k];
+                        int gcr, gcc;
+                        uint32_t vm, in;
+                        where(code, gcr, gcc, vm, in);
+                        if (nq <= 32) ntest += __popc(in);
+                        uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
+                        const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
+                        if (moved) {
+                            mark(gcr, gcc, moved);
+                            if (moved & in) moved_own = true;
+                        }
+                    }
+                    __syncwarp();
                 }
                 if (__syncthreads_or(moved_own) && tid == 0) ctrl->last = g;
-                if (tid == 0) ctrl->lqn = 0;  // every thread read it before the barrier above
             }
             // ---- end of a step: every block's last change, then the stop test
             __syncthreads();
@@ -479,10 +476,42 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(ResArgs P)
     }
 }
 
+// One launch of k_resident<NW>: as many clusters of C blocks as fit at once
+// (each loops over the job queue), at most one per job.
+template <int NW>
+cudaError_t resident_launch(int C, int n, size_t smem, cudaStream_t stream, const ResArgs &P)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_resident<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(NW * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(C);
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<NW>, &cfg);
+    }
+    if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(C * std::min(clusters, n));
+        e = cudaLaunchKernelEx(&cfg, k_resident<NW>, P);
+    }
+    return e;
+}
+
 }  // namespace
 
-// Smallest cluster (1, 2, 4, 8 blocks) whose shared memory holds the image; 0 if none.
-int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_out, int *rp_out)
+// Smallest cluster (1, 2, 4, 8 blocks of nw warps) whose shared memory holds
+// the image; 0 if none.
+int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, int *rows_out, int *rp_out)
 {
     const int es = dtype == THIN_U16 ? 2 : 1;
     const int rp = int((size_t(w) * es + 15) / 16 * 16) + 32;
@@ -492,7 +521,7 @@ int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_
         rows += rows & 1;
         const int held = rows + (C > 1 ? 2 * std::min(kResStep, rows) : 0);  // halo: see resident_run
         if (held / 2 * cw > 65535) continue;  // queue codes are 16-bit
-        if (res_smem_bytes(held, rp, cw, wpr) <= smem_limit) {
+        if (res_smem_bytes(held, rp, wpr, nw) <= smem_limit) {
             if (rows_out) *rows_out = rows;
             if (rp_out) *rp_out = rp;
             return C;
@@ -501,16 +530,21 @@ int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int *rows_
     return 0;
 }
 
-size_t resident_smem_limit()
+// Shared memory a block may take when `blocks` blocks share an SM.
+size_t resident_smem_limit(int blocks)
 {
-    int dev = 0, optin = 0;
+    int dev = 0, optin = 0, per_sm = 0, reserved = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return size_t(optin > 0 ? optin : 48 * 1024);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    size_t lim = size_t(optin > 0 ? optin : 48 * 1024);
+    if (blocks > 1 && per_sm > 0) lim = std::min(lim, size_t(per_sm) / blocks - size_t(reserved));
+    return lim;
 }
 
-// Runs the jobs (all fitting cluster size C) in one launch of k_resident.
-int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+// Runs the jobs (all fitting cluster size C with nw warps a block) in one launch of k_resident.
+int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream, thin_stats *out)
 {
     if (n <= 0) return THIN_OK;
     if (opt.max_phases == 0) {
@@ -523,7 +557,8 @@ int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cud
             }
         return THIN_ERR_NOT_CONVERGED;
     }
-    const size_t limit = resident_smem_limit();
+    if (nw != 4 && nw != 8 && nw != 16) return THIN_ERR_ARG;
+    const size_t limit = resident_smem_limit(kResMaxWarps / nw);
     std::vector<ResJob> rj(n);
     size_t smem = 0;
     for (int k = 0; k < n; ++k) {
@@ -549,7 +584,7 @@ int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cud
         r.bulk = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0) && ((size_t(J.w) * es) % 16 == 0);
         r.index = k;
         const int held = r.rows + 2 * r.hr;
-        const size_t need = res_smem_bytes(held, r.rp, r.cw, r.wpr);
+        const size_t need = res_smem_bytes(held, r.rp, r.wpr, nw);
         if (need > limit || held / 2 * r.cw > 65535) return THIN_ERR_ARG;
         smem = std::max(smem, need);
     }
@@ -595,29 +630,12 @@ int resident_run(const JobSpec *jobs, int n, int C, const thin_options &opt, cud
     P.timeout_ns = 2000000000ull;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
 
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kResThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
     if (e == cudaSuccess) {
-        cfg.gridDim = dim3(C);
-        e = cudaOccupancyMaxActiveClusters(&clusters, k_resident, &cfg);
-    }
-    if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) {
-        cfg.gridDim = dim3(C * std::min(clusters, n));
-        e = cudaLaunchKernelEx(&cfg, k_resident, P);
+        switch (nw) {
+        case 4: e = resident_launch<4>(C, n, smem, stream, P); break;
+        case 8: e = resident_launch<8>(C, n, smem, stream, P); break;
+        default: e = resident_launch<16>(C, n, smem, stream, P); break;
+        }
     }
     int rc = THIN_OK;
     if (e == cudaSuccess && out) {
