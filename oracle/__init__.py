@@ -33,6 +33,8 @@ _lib = None
 
 RULE_MAX = 0  # F^-(c) = max of F over c  (reading R1, default)
 RULE_MIN = 1  # F^-(c) = min of F over c  (reading R2)
+OP_THIN = 0      # lambda-thinning: lower lambda-destructible points
+OP_SKELETON = 1  # lambda-skeleton (Sec. 2.2): lower lambda-deletable points that are not lambda-end
 
 
 class OracleStats(ctypes.Structure):
@@ -70,15 +72,16 @@ def _load():
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.oracle_tplusplus.argtypes = [ctypes.c_uint]
     lib.oracle_lambda_destructible.argtypes = [i32p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int, i32p]
+    lib.oracle_lambda_skeleton_point.argtypes = lib.oracle_lambda_destructible.argtypes
     lib.oracle_thin.argtypes = [i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
-                                ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(OracleStats)]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(OracleStats)]
     lib.oracle_thin_queue.argtypes = [i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
-                                      ctypes.c_uint32, ctypes.c_int]
+                                      ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
     lib.oracle_thin_queue.restype = ctypes.c_int64
     lib.oracle_thin_minvalue.argtypes = lib.oracle_thin_queue.argtypes
     lib.oracle_thin_minvalue.restype = ctypes.c_int64
     lib.oracle_count_lambda_destructible.argtypes = [i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
-                                                     ctypes.c_uint32, ctypes.c_int]
+                                                     ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
     lib.oracle_count_lambda_destructible.restype = ctypes.c_int64
     lib.oracle_count_section_components.argtypes = [i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                      ctypes.c_int32, ctypes.c_int, ctypes.c_int,
@@ -126,43 +129,54 @@ def lambda_destructible(nb, fx: int, lam: int, rule: int = RULE_MAX):
     return bool(r), int(alpha.value)
 
 
-def thin(img, lam: int, rule: int = RULE_MAX, start_phase: int = 0, max_phases: int = -1):
-    """Subfield-schedule lambda-thinning.  Returns (result, stats dict); the
-    result keeps the input's dtype."""
+def lambda_skeleton_point(nb, fx: int, lam: int, rule: int = RULE_MAX):
+    """(lowerable by the lambda-skeleton, alpha^-) for value fx with ring-ordered neighbours nb."""
+    lib = _load()
+    arr = (ctypes.c_int32 * 8)(*[int(v) for v in nb])
+    alpha = ctypes.c_int32(int(fx))
+    r = lib.oracle_lambda_skeleton_point(arr, int(fx), int(lam), int(rule), ctypes.byref(alpha))
+    return bool(r), int(alpha.value)
+
+
+def thin(img, lam: int, rule: int = RULE_MAX, start_phase: int = 0, max_phases: int = -1, op: int = OP_THIN):
+    """Subfield-schedule lambda-thinning (op = OP_THIN) or lambda-skeleton
+    (op = OP_SKELETON).  Returns (result, stats dict); the result keeps the
+    input's dtype."""
     a = _i32(img)
     h, w = a.shape
     st = OracleStats()
-    rc = _load().oracle_thin(_ptr(a), w, h, w, int(lam), int(rule), int(start_phase),
+    rc = _load().oracle_thin(_ptr(a), w, h, w, int(lam), int(rule), int(op), int(start_phase),
                              int(max_phases), ctypes.byref(st))
     d = st.as_dict()
     d["capped"] = bool(rc)
     return a.astype(np.asarray(img).dtype), d
 
 
-def thin_queue(img, lam: int, rule: int = RULE_MAX):
+def thin_queue(img, lam: int, rule: int = RULE_MAX, op: int = OP_THIN):
     """FIFO-order sequential thinning (invariants-only cross-check).  Returns (result, lowered)."""
     a = _i32(img)
     h, w = a.shape
-    n = _load().oracle_thin_queue(_ptr(a), w, h, w, int(lam), int(rule))
+    n = _load().oracle_thin_queue(_ptr(a), w, h, w, int(lam), int(rule), int(op))
     if n < 0:
         raise MemoryError("oracle_thin_queue")
     return a.astype(np.asarray(img).dtype), int(n)
 
 
-def thin_minvalue(img, lam: int, rule: int = RULE_MAX):
+def thin_minvalue(img, lam: int, rule: int = RULE_MAX, op: int = OP_THIN):
     """Minimal-value-first sequential thinning (Sec. 2.2 selection).  Returns (result, lowered)."""
     a = _i32(img)
     h, w = a.shape
-    n = _load().oracle_thin_minvalue(_ptr(a), w, h, w, int(lam), int(rule))
+    n = _load().oracle_thin_minvalue(_ptr(a), w, h, w, int(lam), int(rule), int(op))
     if n < 0:
         raise MemoryError("oracle_thin_minvalue")
     return a.astype(np.asarray(img).dtype), int(n)
 
 
-def count_lambda_destructible(img, lam: int, rule: int = RULE_MAX) -> int:
+def count_lambda_destructible(img, lam: int, rule: int = RULE_MAX, op: int = OP_THIN) -> int:
+    """Interior points the test of ``op`` accepts (0 at a fixed point)."""
     a = _i32(img)
     h, w = a.shape
-    return int(_load().oracle_count_lambda_destructible(_ptr(a), w, h, w, int(lam), int(rule)))
+    return int(_load().oracle_count_lambda_destructible(_ptr(a), w, h, w, int(lam), int(rule), int(op)))
 
 
 def count_section_components(img, k: int, n: int, complement: bool = False, flip=None) -> int:

@@ -164,6 +164,60 @@ int oracle_lambda_destructible(const int32_t nb[8], int32_t fx, uint32_t lambda,
     return 0;
 }
 
+/*
+ * End point for F (Sec. 2.1): x is an end point of the section F_k with
+ * k = F(x), i.e. exactly one point of Gamma_8^*(x) lies in F_k (n = 8).
+ */
+static int end_point(const int32_t nb[8], int32_t fx)
+{
+    int i, c = 0;
+    for (i = 0; i < 8; i++) c += nb[i] >= fx;
+    return c == 1;
+}
+
+/*
+ * The lambda-skeleton's test (Sec. 2.1, algorithm of Sec. 2.2): x may be
+ * lowered when it is lambda-deletable and not lambda-end.
+ *   peak point         <=> T+ = 0 (no neighbour >= F(x));
+ *   lambda-deletable   <=> lambda-destructible, or a peak point with
+ *                          F(x) - alpha^-(x, F) <= lambda;
+ *   lambda-end         <=> an end point for F with F(x) - alpha^-(x, F) > lambda.
+ * Returns 1 if x may be lowered and then stores alpha^-(x, F) in *alpha.
+ */
+int oracle_lambda_skeleton_point(const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
+                                 int32_t *alpha)
+{
+    unsigned lower = 0;
+    int i, tplus, tminus, label[8], deletable, lambda_end;
+    int32_t a = 0, tmp;
+    int have = 0;
+    for (i = 0; i < 8; i++) {
+        if (nb[i] < fx) {
+            lower |= 1u << i;
+            if (!have || nb[i] > a) a = nb[i];
+            have = 1;
+        }
+    }
+    if (!lower) return 0; /* alpha^- = F(x): not destructible, not a peak */
+    oracle_mask_numbers(lower, &tplus, &tminus, label);
+    deletable = oracle_lambda_destructible(nb, fx, lambda, rule, &tmp) ||
+                (tplus == 0 && (int64_t)fx - (int64_t)a <= (int64_t)lambda);
+    lambda_end = end_point(nb, fx) && (int64_t)fx - (int64_t)a > (int64_t)lambda;
+    if (deletable && !lambda_end) {
+        *alpha = a;
+        return 1;
+    }
+    return 0;
+}
+
+/* The test of operator `op`: 0 = lambda-thinning (lambda-destructible
+ * points), 1 = lambda-skeleton (lambda-deletable, not lambda-end points). */
+int oracle_lowerable(int op, const int32_t nb[8], int32_t fx, uint32_t lambda, int rule, int32_t *alpha)
+{
+    return op == 1 ? oracle_lambda_skeleton_point(nb, fx, lambda, rule, alpha)
+                   : oracle_lambda_destructible(nb, fx, lambda, rule, alpha);
+}
+
 static void gather(const int32_t *F, int64_t stride, int x, int y, int32_t nb[8])
 {
     int i;
@@ -181,14 +235,15 @@ typedef struct {
 
 /*
  * Sequential lambda-thinning in the subfield schedule (the lowering loop of
- * Sec. 2.2 with the lambda-destructible predicate of Sec. 2.1).  Rounds of
+ * Sec. 2.2 with the lambda-destructible predicate of Sec. 2.1; op = 1 takes
+ * the lambda-skeleton's test instead, see oracle_lowerable).  Rounds of
  * four consecutive phases start at global phase index start_phase; phase g
  * visits, in raster order, the interior points of parity g mod 4 and lowers
  * each one to alpha^- while it stays lambda-destructible.  Stops after a
  * round with no change, or when max_phases phases have run (max_phases < 0:
  * no cap).  F is modified in place.  Returns 0, or 1 if stopped by the cap.
  */
-int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule,
+int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op,
                 int64_t start_phase, int64_t max_phases, oracle_stats *st)
 {
     int64_t g = start_phase, run = 0;
@@ -212,7 +267,7 @@ int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int r
                     int32_t *fx = &F[(int64_t)y * stride + x];
                     if (2 * (y & 1) + (x & 1) != p) continue;
                     gather(F, stride, x, y, nb);
-                    while (oracle_lambda_destructible(nb, *fx, lambda, rule, &alpha)) {
+                    while (oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) {
                         *fx = alpha;
                         s.lowered++;
                         phase_changed = 1;
@@ -245,7 +300,7 @@ int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int r
  * the subfield schedule; it is compared by invariants only.  Returns the
  * number of lowering steps, or -1 on allocation failure.
  */
-int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule)
+int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op)
 {
     int64_t n = (int64_t)w * h, head = 0, count = 0, lowered = 0;
     int64_t *q;
@@ -277,7 +332,7 @@ int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lam
         y = (int)(id / w);
         fx = &F[(int64_t)y * stride + x];
         gather(F, stride, x, y, nb);
-        while (oracle_lambda_destructible(nb, *fx, lambda, rule, &alpha)) {
+        while (oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) {
             *fx = alpha;
             lowered++;
             moved = 1;
@@ -332,14 +387,15 @@ static heap_item heap_pop(heap_item *hp, int64_t *n)
 
 /*
  * Minimal-value sequential thinning (the selection rule of the algorithm of
- * Sec. 2.2): repeatedly take, among the lambda-destructible points, one of
- * minimal value (ties: smallest raster index) and lower it to alpha^-.
+ * Sec. 2.2): repeatedly take, among the points the test of `op` accepts, one
+ * of minimal value (ties: smallest raster index) and lower it to alpha^-.
+ * With op = 1 this is the paper's lambda-skeleton algorithm itself.
  * Candidates sit in a lazy min-heap; a popped entry whose value is stale is
  * dropped, and each lowering re-queues the point and its eight neighbours.
  * Compared with the subfield schedule by invariants only.  Returns the number
  * of lowering steps, or -1 on allocation failure.
  */
-int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule)
+int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op)
 {
     int64_t cap, n = 0, lowered = 0;
     heap_item *hp;
@@ -363,7 +419,7 @@ int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t 
         fx = &F[(int64_t)y * stride + x];
         if (*fx != it.v) continue; /* stale entry */
         gather(F, stride, x, y, nb);
-        if (!oracle_lambda_destructible(nb, *fx, lambda, rule, &alpha)) continue;
+        if (!oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) continue;
         *fx = alpha;
         lowered++;
         if (n + 9 > cap) {
@@ -391,9 +447,9 @@ int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t 
     return lowered;
 }
 
-/* Number of interior points that are lambda-destructible for F (0 at a fixed point). */
+/* Number of interior points the test of `op` accepts for F (0 at a fixed point). */
 int64_t oracle_count_lambda_destructible(const int32_t *F, int w, int h, int64_t stride,
-                                         uint32_t lambda, int rule)
+                                         uint32_t lambda, int rule, int op)
 {
     int64_t c = 0;
     int x, y;
@@ -401,7 +457,7 @@ int64_t oracle_count_lambda_destructible(const int32_t *F, int w, int h, int64_t
         for (x = 1; x < w - 1; x++) {
             int32_t nb[8], alpha;
             gather(F, stride, x, y, nb);
-            if (oracle_lambda_destructible(nb, F[(int64_t)y * stride + x], lambda, rule, &alpha)) c++;
+            if (oracle_lowerable(op, nb, F[(int64_t)y * stride + x], lambda, rule, &alpha)) c++;
         }
     return c;
 }

@@ -64,6 +64,25 @@ def point_step(grid, lam, rule):
     return False, alpha
 
 
+def skeleton_step(grid, lam, rule):
+    """(lowerable by the lambda-skeleton, alpha) of the centre of a 3x3 grid,
+    from the definitions of Sec. 2.1: lambda-deletable (lambda-destructible, or
+    a peak point -- no neighbour in F_k, k = F(x) -- with F(x) - alpha <= lam)
+    and not lambda-end (an end point -- exactly one neighbour in F_k -- with
+    F(x) - alpha > lam)."""
+    g = np.asarray(grid, dtype=np.int64)
+    c = int(g[1, 1])
+    in_section = [int(v) >= c for (r, cc), v in np.ndenumerate(g) if (r, cc) != (1, 1)]
+    lower = [int(v) for (r, cc), v in np.ndenumerate(g) if (r, cc) != (1, 1) and v < c]
+    if not lower:
+        return False, c
+    alpha = max(lower)
+    tplus = local_numbers(g)[0]
+    deletable = point_step(g, lam, rule)[0] or (tplus == 0 and c - alpha <= lam)
+    lambda_end = sum(in_section) == 1 and c - alpha > lam
+    return deletable and not lambda_end, alpha
+
+
 def components(mask, structure):
     return ndimage.label(mask, structure=structure)[1]
 
@@ -80,11 +99,13 @@ def global_destructible(img, x, y):
             components(~X, FOUR) == components(~Xm, FOUR))
 
 
-def schedule(img, lam, rule=0, use_global=False, max_rounds=10000):
+def schedule(img, lam, rule=0, use_global=False, max_rounds=10000, op=0):
     """Subfield-schedule thinning in plain Python: phases 0,1,2,3,... visit the
     interior points of parity 2(y&1)+(x&1); each is lowered to alpha^- while it
-    is lambda-destructible (use_global: destructible by global component
-    counts, lambda = 0 only).  Stops after a round with no change."""
+    is lambda-destructible (op 0) or lambda-deletable and not lambda-end (op 1)
+    (use_global: destructible by global component counts, lambda = 0 only;
+    with op 1 an end point -- one neighbour in F_k -- is then kept).  Stops
+    after a round with no change."""
     a = np.asarray(img, dtype=np.int64).copy()
     h, w = a.shape
     for _ in range(max_rounds):
@@ -99,7 +120,11 @@ def schedule(img, lam, rule=0, use_global=False, max_rounds=10000):
                         if use_global:
                             lower = [int(v) for (r, c), v in np.ndenumerate(g) if (r, c) != (1, 1) and v < g[1, 1]]
                             ok = bool(lower) and global_destructible(a, x, y)
+                            if op == 1:
+                                ok = ok and int((g >= g[1, 1]).sum()) - 1 != 1
                             alpha = max(lower) if lower else int(g[1, 1])
+                        elif op == 1:
+                            ok, alpha = skeleton_step(g, lam, rule)
                         else:
                             ok, alpha = point_step(g, lam, rule)
                         if not ok:

@@ -296,3 +296,115 @@ def test_oracle_leaves_inputs_untouched():
         oracle.thin_queue(img, 3)
         oracle.thin_minvalue(img, 3)
         assert np.array_equal(img, keep)
+
+
+# ---------------------------------------------------------------- lambda-skeleton (Sec. 2.2)
+
+SK = oracle.OP_SKELETON
+
+
+def test_skeleton_point_against_reference():
+    rng = np.random.default_rng(31)
+    for _ in range(4000):
+        g = rng.integers(0, 7, (3, 3))
+        if rng.random() < 0.2:  # more end points: one neighbour at or above the centre
+            g[:] = rng.integers(0, 3)
+            g[1, 1] = 5
+            r, c = bf.RING_RC[int(rng.integers(8))]
+            g[r, c] = int(rng.integers(5, 7))
+        nb = bf.ring_values(g)
+        for lam in (0, 1, 2, 4, 6):
+            for rule in (0, 1):
+                got = oracle.lambda_skeleton_point(nb, g[1, 1], lam, rule)
+                ref = bf.skeleton_step(g, lam, rule)
+                assert got[0] == ref[0], (g, lam, rule)
+                if got[0]:
+                    assert got[1] == ref[1]
+
+
+@pytest.mark.parametrize("lam,rule", [(0, 0), (1, 0), (3, 0), (2, 1)])
+def test_skeleton_schedule_against_python_reference(lam, rule):
+    rng = np.random.default_rng(200 + lam + 10 * rule)
+    for _ in range(12):
+        h, w = int(rng.integers(3, 9)), int(rng.integers(3, 10))
+        img = rng.integers(0, 5, (h, w)).astype(np.int32)
+        out, st = oracle.thin(img, lam, rule, op=SK)
+        assert np.array_equal(out, bf.schedule(img, lam, rule, op=1)), img
+        assert st["converged"] == 1
+
+
+def test_skeleton_lambda0_against_global_brute_force():
+    """At lambda = 0 the skeleton lowers destructible points that are not end
+    points (Sec. 2.2, first sentence); destructibility by global counts."""
+    rng = np.random.default_rng(22)
+    for _ in range(10):
+        h, w = int(rng.integers(4, 8)), int(rng.integers(4, 8))
+        img = rng.integers(0, 4, (h, w)).astype(np.int32)
+        out, _ = oracle.thin(img, 0, op=SK)
+        assert np.array_equal(out, bf.schedule(img, 0, use_global=True, op=1)), img
+
+
+@pytest.mark.parametrize("d,lam", [(40, 0), (40, 39), (40, 40), (40, 80)])
+@pytest.mark.parametrize("diag", [False, True])
+def test_skeleton_keeps_a_line_iff_its_contrast_exceeds_lambda(d, lam, diag):
+    """A one-pixel line of contrast d on a flat background: every inner pixel
+    is not simple and both ends are end points, so the skeleton keeps the line
+    while d > lambda (its ends are lambda-end); once d <= lambda the ends are
+    lambda-deletable and the line is eaten down to the background.  Plain
+    lambda-thinning (d > lambda) erodes the line from its ends to a single
+    peak pixel."""
+    img = np.full((20, 20), 100, np.int32)
+    for k in range(3, 16):
+        if diag:
+            img[k, k] = 100 + d
+        else:
+            img[9, k] = 100 + d
+    out, _ = oracle.thin(img, lam, op=SK)
+    if d > lam:
+        assert np.array_equal(out, img)
+    else:
+        assert (out == 100).all()
+    if d > lam:
+        thin_out, _ = oracle.thin(img, lam)
+        assert (thin_out == 100 + d).sum() == 1 and (thin_out > 100).sum() == 1
+
+
+@pytest.mark.parametrize("d,lam", [(5, 4), (5, 5), (5, 9)])
+def test_skeleton_removes_a_peak_iff_its_height_le_lambda(d, lam):
+    img = np.full((9, 9), 50, np.int32)
+    img[4, 4] = 50 + d
+    out, _ = oracle.thin(img, lam, op=SK)
+    assert out[4, 4] == (50 if d <= lam else 50 + d)
+    assert oracle.thin(img, lam)[0][4, 4] == 50 + d  # a peak is never lambda-destructible
+
+
+def _skeleton_invariants(img, out, lam):
+    assert (out <= img).all()
+    assert oracle.count_lambda_destructible(out, lam, op=SK) == 0
+    b = np.ones(img.shape, bool)
+    b[1:-1, 1:-1] = False
+    assert (out[b] == img[b]).all()
+
+
+@pytest.mark.parametrize("lam", [0, 5, 20])
+def test_skeleton_invariants_on_generator_images(lam):
+    img = value_noise_image(40, 56, "u8", seed=17)
+    out, st = oracle.thin(img, lam, op=SK)
+    _skeleton_invariants(img, out, lam)
+    assert st["converged"] == 1 and st["lowered"] > 0
+    thin_out, _ = oracle.thin(img, lam)
+    assert (out >= thin_out).sum() > (out < thin_out).sum()  # end points kept: mostly above the thinning
+    if lam == 0:  # only destructible points move at lambda = 0: every section keeps its topology
+        levels = sorted(oracle.level_topology(img))
+        assert oracle.level_topology(out, levels) == oracle.level_topology(img, levels)
+
+
+@pytest.mark.parametrize("lam", [0, 10])
+def test_paper_minvalue_skeleton_invariants(lam):
+    """The paper's own algorithm (minimal value first, Sec. 2.2) reaches a
+    fixed point with the same invariants; its image may differ."""
+    img = value_noise_image(30, 44, "u8", seed=19)
+    out, n = oracle.thin_minvalue(img, lam, op=SK)
+    _skeleton_invariants(img, out, lam)
+    qout, _ = oracle.thin_queue(img, lam, op=SK)
+    _skeleton_invariants(img, qout, lam)
