@@ -1,5 +1,5 @@
 /*
- * CPU oracle for grayscale lambda-thinning under (8,4)-adjacency.
+ * CPU oracle for grayscale lambda-thinning under (8,4)-adjacency (and (4,8)).
  *
  * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded restatement
  * of the paper's definitions (Sec. 2.1) and of its lowering loop (Sec. 2.2),
@@ -93,17 +93,24 @@ static int count_components(unsigned S, int n, int label[8])
 /*
  * Connectivity numbers of Sec. 2.1 for a point whose strictly lower
  * neighbours (Gamma^--) form the ring mask `lower`; the neighbours that are
- * greater or equal (Gamma^+) are the rest.  n = 8 for sections of F and
- * nbar = 4 for their complements.
- *   T+  = #C_8[x, Gamma^+]        T-- = #C_4[x, Gamma^--]
+ * greater or equal (Gamma^+) are the rest.  adj 0 is the pair (n, nbar) =
+ * (8, 4): n = 8 for sections of F, nbar = 4 for their complements; adj 1 is
+ * (4, 8).
+ *   T+  = #C_n[x, Gamma^+]        T-- = #C_nbar[x, Gamma^--]
  * label[] gets the T-- component of each neighbour (-1 if none).
  */
-int oracle_mask_numbers(unsigned lower, int *tplus, int *tminus, int label[8])
+int oracle_mask_numbers_adj(int adj, unsigned lower, int *tplus, int *tminus, int label[8])
 {
     unsigned plus = (~lower) & 0xffu;
-    *tplus = count_components(plus, 8, 0);
-    *tminus = count_components(lower & 0xffu, 4, label);
+    const int n = adj ? 4 : 8, nbar = adj ? 8 : 4;
+    *tplus = count_components(plus, n, 0);
+    *tminus = count_components(lower & 0xffu, nbar, label);
     return 0;
+}
+
+int oracle_mask_numbers(unsigned lower, int *tplus, int *tminus, int label[8])
+{
+    return oracle_mask_numbers_adj(0, lower, tplus, tminus, label);
 }
 
 /* T++ = #C_8[x, Gamma^++] for the strictly greater neighbours (Sec. 2.1). */
@@ -123,8 +130,8 @@ int oracle_tplusplus(unsigned greater)
  * Returns 1 if lambda-destructible and then stores alpha^-(x, F), the
  * largest value over Gamma^-- (Sec. 2.1), in *alpha.
  */
-int oracle_lambda_destructible(const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
-                               int32_t *alpha)
+int oracle_lambda_destructible_adj(int adj, const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
+                                   int32_t *alpha)
 {
     unsigned lower = 0;
     int i, tplus, tminus, label[8];
@@ -138,7 +145,7 @@ int oracle_lambda_destructible(const int32_t nb[8], int32_t fx, uint32_t lambda,
         }
     }
     if (!lower) return 0; /* Gamma^-- empty: T-- = 0 */
-    oracle_mask_numbers(lower, &tplus, &tminus, label);
+    oracle_mask_numbers_adj(adj, lower, &tplus, &tminus, label);
     if (tplus == 1 && tminus == 1) {
         *alpha = a;
         return 1;
@@ -164,14 +171,22 @@ int oracle_lambda_destructible(const int32_t nb[8], int32_t fx, uint32_t lambda,
     return 0;
 }
 
+int oracle_lambda_destructible(const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
+                               int32_t *alpha)
+{
+    return oracle_lambda_destructible_adj(0, nb, fx, lambda, rule, alpha);
+}
+
 /*
  * End point for F (Sec. 2.1): x is an end point of the section F_k with
- * k = F(x), i.e. exactly one point of Gamma_8^*(x) lies in F_k (n = 8).
+ * k = F(x), i.e. exactly one point of Gamma_n^*(x) lies in F_k (n = 8 for
+ * adj 0, n = 4 for adj 1).
  */
-static int end_point(const int32_t nb[8], int32_t fx)
+static int end_point(int adj, const int32_t nb[8], int32_t fx)
 {
     int i, c = 0;
-    for (i = 0; i < 8; i++) c += nb[i] >= fx;
+    for (i = 0; i < 8; i++)
+        if (adjacent(adj ? 4 : 8, RING_DX[i], RING_DY[i], 0, 0)) c += nb[i] >= fx;
     return c == 1;
 }
 
@@ -184,8 +199,8 @@ static int end_point(const int32_t nb[8], int32_t fx)
  *   lambda-end         <=> an end point for F with F(x) - alpha^-(x, F) > lambda.
  * Returns 1 if x may be lowered and then stores alpha^-(x, F) in *alpha.
  */
-int oracle_lambda_skeleton_point(const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
-                                 int32_t *alpha)
+int oracle_lambda_skeleton_point_adj(int adj, const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
+                                     int32_t *alpha)
 {
     unsigned lower = 0;
     int i, tplus, tminus, label[8], deletable, lambda_end;
@@ -199,10 +214,10 @@ int oracle_lambda_skeleton_point(const int32_t nb[8], int32_t fx, uint32_t lambd
         }
     }
     if (!lower) return 0; /* alpha^- = F(x): not destructible, not a peak */
-    oracle_mask_numbers(lower, &tplus, &tminus, label);
-    deletable = oracle_lambda_destructible(nb, fx, lambda, rule, &tmp) ||
+    oracle_mask_numbers_adj(adj, lower, &tplus, &tminus, label);
+    deletable = oracle_lambda_destructible_adj(adj, nb, fx, lambda, rule, &tmp) ||
                 (tplus == 0 && (int64_t)fx - (int64_t)a <= (int64_t)lambda);
-    lambda_end = end_point(nb, fx) && (int64_t)fx - (int64_t)a > (int64_t)lambda;
+    lambda_end = end_point(adj, nb, fx) && (int64_t)fx - (int64_t)a > (int64_t)lambda;
     if (deletable && !lambda_end) {
         *alpha = a;
         return 1;
@@ -210,12 +225,19 @@ int oracle_lambda_skeleton_point(const int32_t nb[8], int32_t fx, uint32_t lambd
     return 0;
 }
 
-/* The test of operator `op`: 0 = lambda-thinning (lambda-destructible
- * points), 1 = lambda-skeleton (lambda-deletable, not lambda-end points). */
-int oracle_lowerable(int op, const int32_t nb[8], int32_t fx, uint32_t lambda, int rule, int32_t *alpha)
+int oracle_lambda_skeleton_point(const int32_t nb[8], int32_t fx, uint32_t lambda, int rule,
+                                 int32_t *alpha)
 {
-    return op == 1 ? oracle_lambda_skeleton_point(nb, fx, lambda, rule, alpha)
-                   : oracle_lambda_destructible(nb, fx, lambda, rule, alpha);
+    return oracle_lambda_skeleton_point_adj(0, nb, fx, lambda, rule, alpha);
+}
+
+/* The test of operator `op` under adjacency pair `adj` (0: (8,4), 1: (4,8)):
+ * op 0 = lambda-thinning (lambda-destructible points), op 1 = lambda-skeleton
+ * (lambda-deletable, not lambda-end points). */
+int oracle_lowerable(int op, int adj, const int32_t nb[8], int32_t fx, uint32_t lambda, int rule, int32_t *alpha)
+{
+    return op == 1 ? oracle_lambda_skeleton_point_adj(adj, nb, fx, lambda, rule, alpha)
+                   : oracle_lambda_destructible_adj(adj, nb, fx, lambda, rule, alpha);
 }
 
 static void gather(const int32_t *F, int64_t stride, int x, int y, int32_t nb[8])
@@ -243,7 +265,7 @@ typedef struct {
  * round with no change, or when max_phases phases have run (max_phases < 0:
  * no cap).  F is modified in place.  Returns 0, or 1 if stopped by the cap.
  */
-int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op,
+int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op, int adj,
                 int64_t start_phase, int64_t max_phases, oracle_stats *st)
 {
     int64_t g = start_phase, run = 0;
@@ -267,7 +289,7 @@ int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int r
                     int32_t *fx = &F[(int64_t)y * stride + x];
                     if (2 * (y & 1) + (x & 1) != p) continue;
                     gather(F, stride, x, y, nb);
-                    while (oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) {
+                    while (oracle_lowerable(op, adj, nb, *fx, lambda, rule, &alpha)) {
                         *fx = alpha;
                         s.lowered++;
                         phase_changed = 1;
@@ -300,7 +322,7 @@ int oracle_thin(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int r
  * the subfield schedule; it is compared by invariants only.  Returns the
  * number of lowering steps, or -1 on allocation failure.
  */
-int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op)
+int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op, int adj)
 {
     int64_t n = (int64_t)w * h, head = 0, count = 0, lowered = 0;
     int64_t *q;
@@ -332,7 +354,7 @@ int64_t oracle_thin_queue(int32_t *F, int w, int h, int64_t stride, uint32_t lam
         y = (int)(id / w);
         fx = &F[(int64_t)y * stride + x];
         gather(F, stride, x, y, nb);
-        while (oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) {
+        while (oracle_lowerable(op, adj, nb, *fx, lambda, rule, &alpha)) {
             *fx = alpha;
             lowered++;
             moved = 1;
@@ -395,7 +417,7 @@ static heap_item heap_pop(heap_item *hp, int64_t *n)
  * Compared with the subfield schedule by invariants only.  Returns the number
  * of lowering steps, or -1 on allocation failure.
  */
-int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op)
+int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t lambda, int rule, int op, int adj)
 {
     int64_t cap, n = 0, lowered = 0;
     heap_item *hp;
@@ -419,7 +441,7 @@ int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t 
         fx = &F[(int64_t)y * stride + x];
         if (*fx != it.v) continue; /* stale entry */
         gather(F, stride, x, y, nb);
-        if (!oracle_lowerable(op, nb, *fx, lambda, rule, &alpha)) continue;
+        if (!oracle_lowerable(op, adj, nb, *fx, lambda, rule, &alpha)) continue;
         *fx = alpha;
         lowered++;
         if (n + 9 > cap) {
@@ -449,7 +471,7 @@ int64_t oracle_thin_minvalue(int32_t *F, int w, int h, int64_t stride, uint32_t 
 
 /* Number of interior points the test of `op` accepts for F (0 at a fixed point). */
 int64_t oracle_count_lambda_destructible(const int32_t *F, int w, int h, int64_t stride,
-                                         uint32_t lambda, int rule, int op)
+                                         uint32_t lambda, int rule, int op, int adj)
 {
     int64_t c = 0;
     int x, y;
@@ -457,7 +479,7 @@ int64_t oracle_count_lambda_destructible(const int32_t *F, int w, int h, int64_t
         for (x = 1; x < w - 1; x++) {
             int32_t nb[8], alpha;
             gather(F, stride, x, y, nb);
-            if (oracle_lowerable(op, nb, F[(int64_t)y * stride + x], lambda, rule, &alpha)) c++;
+            if (oracle_lowerable(op, adj, nb, F[(int64_t)y * stride + x], lambda, rule, &alpha)) c++;
         }
     return c;
 }
@@ -518,17 +540,24 @@ int64_t oracle_count_section_components(const int32_t *F, int w, int h, int64_t 
 
 /*
  * Brute-force global destructibility of the point (x, y): with k = F(x),
- * removing x from F_k keeps the number of 8-components of F_k and the number
- * of 4-components of its complement (a simple point changes neither,
- * Sec. 2.1).  Returns 1 if both counts are kept, 0 if not, -1 on error.
+ * removing x from F_k keeps the number of n-components of F_k and the number
+ * of nbar-components of its complement (a simple point changes neither,
+ * Sec. 2.1); (n, nbar) = (8, 4) for adj 0, (4, 8) for adj 1.  Returns 1 if
+ * both counts are kept, 0 if not, -1 on error.
  */
-int oracle_global_destructible(const int32_t *F, int w, int h, int64_t stride, int x, int y)
+int oracle_global_destructible_adj(int adj, const int32_t *F, int w, int h, int64_t stride, int x, int y)
 {
     int32_t k = F[(int64_t)y * stride + x];
-    int64_t a = oracle_count_section_components(F, w, h, stride, k, 8, 0, -1, -1);
-    int64_t b = oracle_count_section_components(F, w, h, stride, k, 8, 0, x, y);
-    int64_t c = oracle_count_section_components(F, w, h, stride, k, 4, 1, -1, -1);
-    int64_t d = oracle_count_section_components(F, w, h, stride, k, 4, 1, x, y);
+    const int n = adj ? 4 : 8, nbar = adj ? 8 : 4;
+    int64_t a = oracle_count_section_components(F, w, h, stride, k, n, 0, -1, -1);
+    int64_t b = oracle_count_section_components(F, w, h, stride, k, n, 0, x, y);
+    int64_t c = oracle_count_section_components(F, w, h, stride, k, nbar, 1, -1, -1);
+    int64_t d = oracle_count_section_components(F, w, h, stride, k, nbar, 1, x, y);
     if (a < 0 || b < 0 || c < 0 || d < 0) return -1;
     return a == b && c == d;
+}
+
+int oracle_global_destructible(const int32_t *F, int w, int h, int64_t stride, int x, int y)
+{
+    return oracle_global_destructible_adj(0, F, w, h, stride, x, y);
 }

@@ -27,29 +27,36 @@ def grid_from_ring(center, nb):
     return g
 
 
-def local_numbers(grid):
-    """(T+, T--, list of lower components as sets of (r, c)) by scipy labelling."""
+def _counted(labels, n_labels, n):
+    """Components (sets of (r, c)) holding a point n-adjacent to the centre."""
+    out = []
+    for lab in range(1, n_labels + 1):
+        pts = set(zip(*np.nonzero(labels == lab)))
+        if n == 8 or pts & FOUR_NEIGHBOURS_RC:
+            out.append(pts)
+    return out
+
+
+def local_numbers(grid, adj=0):
+    """(T+, T--, list of lower components as sets of (r, c)) by scipy labelling;
+    adj 0: (n, nbar) = (8, 4), adj 1: (4, 8)."""
     g = np.asarray(grid, dtype=np.int64)
     c = g[1, 1]
+    n, nbar = (4, 8) if adj else (8, 4)
     upper = (g >= c)
     upper[1, 1] = False
     lower = (g < c)
     lower[1, 1] = False
-    lu, nu = ndimage.label(upper, structure=EIGHT)
-    ll, nl = ndimage.label(lower, structure=FOUR)
-    comps = []
-    for lab in range(1, nl + 1):
-        pts = set(zip(*np.nonzero(ll == lab)))
-        if pts & FOUR_NEIGHBOURS_RC:
-            comps.append(pts)
-    return nu, len(comps), comps
+    lu, nu = ndimage.label(upper, structure=FOUR if n == 4 else EIGHT)
+    ll, nl = ndimage.label(lower, structure=FOUR if nbar == 4 else EIGHT)
+    return len(_counted(lu, nu, n)), len(_counted(ll, nl, nbar)), _counted(ll, nl, nbar)
 
 
-def point_step(grid, lam, rule):
+def point_step(grid, lam, rule, adj=0):
     """(lambda_destructible, alpha) of the centre of a 3x3 grid, from the definitions."""
     g = np.asarray(grid, dtype=np.int64)
     c = int(g[1, 1])
-    tplus, tminus, comps = local_numbers(g)
+    tplus, tminus, comps = local_numbers(g, adj)
     lower = [(r, cc) for r in range(3) for cc in range(3) if (r, cc) != (1, 1) and g[r, cc] < c]
     if not lower:
         return False, c
@@ -64,7 +71,7 @@ def point_step(grid, lam, rule):
     return False, alpha
 
 
-def skeleton_step(grid, lam, rule):
+def skeleton_step(grid, lam, rule, adj=0):
     """(lowerable by the lambda-skeleton, alpha) of the centre of a 3x3 grid,
     from the definitions of Sec. 2.1: lambda-deletable (lambda-destructible, or
     a peak point -- no neighbour in F_k, k = F(x) -- with F(x) - alpha <= lam)
@@ -72,13 +79,14 @@ def skeleton_step(grid, lam, rule):
     F(x) - alpha > lam)."""
     g = np.asarray(grid, dtype=np.int64)
     c = int(g[1, 1])
-    in_section = [int(v) >= c for (r, cc), v in np.ndenumerate(g) if (r, cc) != (1, 1)]
+    near = FOUR_NEIGHBOURS_RC if adj else {rc for rc in RING_RC}  # Gamma_n^*(x)
+    in_section = [int(v) >= c for (r, cc), v in np.ndenumerate(g) if (r, cc) in near]
     lower = [int(v) for (r, cc), v in np.ndenumerate(g) if (r, cc) != (1, 1) and v < c]
     if not lower:
         return False, c
     alpha = max(lower)
-    tplus = local_numbers(g)[0]
-    deletable = point_step(g, lam, rule)[0] or (tplus == 0 and c - alpha <= lam)
+    tplus = local_numbers(g, adj)[0]
+    deletable = point_step(g, lam, rule, adj)[0] or (tplus == 0 and c - alpha <= lam)
     lambda_end = sum(in_section) == 1 and c - alpha > lam
     return deletable and not lambda_end, alpha
 
@@ -87,19 +95,20 @@ def components(mask, structure):
     return ndimage.label(mask, structure=structure)[1]
 
 
-def global_destructible(img, x, y):
-    """Removing (x, y) from F_k, k = F(x, y), keeps #8-components of F_k and
-    #4-components of its complement (scipy labelling on the finite grid)."""
+def global_destructible(img, x, y, adj=0):
+    """Removing (x, y) from F_k, k = F(x, y), keeps #n-components of F_k and
+    #nbar-components of its complement (scipy labelling on the finite grid)."""
     a = np.asarray(img, dtype=np.int64)
     k = a[y, x]
     X = a >= k
     Xm = X.copy()
     Xm[y, x] = False
-    return (components(X, EIGHT) == components(Xm, EIGHT) and
-            components(~X, FOUR) == components(~Xm, FOUR))
+    sn, snbar = (FOUR, EIGHT) if adj else (EIGHT, FOUR)
+    return (components(X, sn) == components(Xm, sn) and
+            components(~X, snbar) == components(~Xm, snbar))
 
 
-def schedule(img, lam, rule=0, use_global=False, max_rounds=10000, op=0):
+def schedule(img, lam, rule=0, use_global=False, max_rounds=10000, op=0, adj=0):
     """Subfield-schedule thinning in plain Python: phases 0,1,2,3,... visit the
     interior points of parity 2(y&1)+(x&1); each is lowered to alpha^- while it
     is lambda-destructible (op 0) or lambda-deletable and not lambda-end (op 1)
@@ -119,14 +128,15 @@ def schedule(img, lam, rule=0, use_global=False, max_rounds=10000, op=0):
                         g = a[y - 1:y + 2, x - 1:x + 2]
                         if use_global:
                             lower = [int(v) for (r, c), v in np.ndenumerate(g) if (r, c) != (1, 1) and v < g[1, 1]]
-                            ok = bool(lower) and global_destructible(a, x, y)
+                            ok = bool(lower) and global_destructible(a, x, y, adj)
                             if op == 1:
-                                ok = ok and int((g >= g[1, 1]).sum()) - 1 != 1
+                                near = FOUR_NEIGHBOURS_RC if adj else set(RING_RC)
+                                ok = ok and sum(int(g[rc] >= g[1, 1]) for rc in near) != 1
                             alpha = max(lower) if lower else int(g[1, 1])
                         elif op == 1:
-                            ok, alpha = skeleton_step(g, lam, rule)
+                            ok, alpha = skeleton_step(g, lam, rule, adj)
                         else:
-                            ok, alpha = point_step(g, lam, rule)
+                            ok, alpha = point_step(g, lam, rule, adj)
                         if not ok:
                             break
                         a[y, x] = alpha

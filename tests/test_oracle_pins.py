@@ -408,3 +408,106 @@ def test_paper_minvalue_skeleton_invariants(lam):
     _skeleton_invariants(img, out, lam)
     qout, _ = oracle.thin_queue(img, lam, op=SK)
     _skeleton_invariants(img, qout, lam)
+
+
+# ---------------------------------------------------------------- (4,8)-adjacency (Sec. 2.1)
+
+A48 = oracle.ADJ_4_8
+
+
+def test_48_all_masks_against_scipy_labelling():
+    for m in range(256):
+        g = bf.grid_from_ring(1, [0 if (m >> i) & 1 else 2 for i in range(8)])
+        tp_ref, tm_ref, comps = bf.local_numbers(g, adj=1)
+        tp, tm, lab = oracle.mask_numbers(m, adj=A48)
+        assert (tp, tm) == (tp_ref, tm_ref), m
+        got = {}
+        for i, l in enumerate(lab):
+            if l >= 0:
+                got.setdefault(l, set()).add(bf.RING_RC[i])
+        assert {frozenset(x) for x in got.values()} == {frozenset(c) for c in comps}, m
+
+
+def test_48_identity_all_masks():
+    """(4,8) in 2-D: T+ = T-- except when no neighbour is lower (T+ = 1,
+    T-- = 0) and when every 4-neighbour is lower (T+ = 0, T-- = 1)."""
+    four = 0b01010101
+    for m in range(256):
+        tp, tm, _ = oracle.mask_numbers(m, adj=A48)
+        if m == 0:
+            assert (tp, tm) == (1, 0)
+        elif m & four == four:
+            assert (tp, tm) == (0, 1), m
+        else:
+            assert tp == tm, m
+
+
+@pytest.mark.parametrize("outer", ["zeros", "ones", "twos", "random"])
+def test_48_local_equals_global_all_masks(outer):
+    rng = np.random.default_rng(15)
+    for m in range(256):
+        img = {"zeros": np.zeros((5, 5)), "ones": np.ones((5, 5)), "twos": np.full((5, 5), 2),
+               "random": rng.integers(0, 3, (5, 5))}[outer].astype(np.int32)
+        img[1:4, 1:4] = bf.grid_from_ring(1, [0 if (m >> i) & 1 else 2 for i in range(8)])
+        local, _ = oracle.lowerable(bf.ring_values(img[1:4, 1:4]), 1, 0, adj=A48)
+        assert local == oracle.global_destructible(img, 2, 2, adj=A48) == bf.global_destructible(img, 2, 2, adj=1), \
+            (m, outer)
+
+
+def test_48_local_equals_global_random_images():
+    rng = np.random.default_rng(41)
+    for _ in range(1200):
+        img = rng.integers(0, 3, (5, 5)).astype(np.int32)
+        for y in range(1, 4):
+            for x in range(1, 4):
+                local, _ = oracle.lowerable(bf.ring_values(img[y - 1:y + 2, x - 1:x + 2]), img[y, x], 0, adj=A48)
+                assert local == oracle.global_destructible(img, x, y, adj=A48), (img, x, y)
+
+
+def test_48_point_tests_against_reference():
+    rng = np.random.default_rng(43)
+    for _ in range(3000):
+        g = rng.integers(0, 7, (3, 3))
+        nb = bf.ring_values(g)
+        for lam in (0, 2, 4):
+            for rule in (0, 1):
+                for op, ref_fn in ((oracle.OP_THIN, bf.point_step), (oracle.OP_SKELETON, bf.skeleton_step)):
+                    got = oracle.lowerable(nb, g[1, 1], lam, rule, op=op, adj=A48)
+                    ref = ref_fn(g, lam, rule, adj=1)
+                    assert got[0] == ref[0], (g, lam, rule, op)
+                    if got[0]:
+                        assert got[1] == ref[1]
+
+
+@pytest.mark.parametrize("lam,op", [(0, 0), (2, 0), (0, 1), (3, 1)])
+def test_48_schedule_against_python_reference(lam, op):
+    rng = np.random.default_rng(300 + lam + 10 * op)
+    for _ in range(10):
+        h, w = int(rng.integers(3, 9)), int(rng.integers(3, 10))
+        img = rng.integers(0, 5, (h, w)).astype(np.int32)
+        out, st = oracle.thin(img, lam, op=op, adj=A48)
+        assert np.array_equal(out, bf.schedule(img, lam, op=op, adj=1)), img
+        assert st["converged"] == 1
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_48_lambda0_against_global_brute_force(op):
+    rng = np.random.default_rng(23 + op)
+    for _ in range(8):
+        h, w = int(rng.integers(4, 8)), int(rng.integers(4, 8))
+        img = rng.integers(0, 4, (h, w)).astype(np.int32)
+        out, _ = oracle.thin(img, 0, op=op, adj=A48)
+        assert np.array_equal(out, bf.schedule(img, 0, use_global=True, op=op, adj=1)), img
+
+
+@pytest.mark.parametrize("lam", [0, 8])
+def test_48_invariants_and_topology(lam):
+    img = value_noise_image(36, 50, "u8", seed=27)
+    out, st = oracle.thin(img, lam, adj=A48)
+    assert (out <= img).all() and st["converged"] == 1 and st["lowered"] > 0
+    assert oracle.count_lambda_destructible(out, lam, adj=A48) == 0
+    if lam == 0:
+        levels = sorted(oracle.level_topology(img, adj=A48))
+        assert oracle.level_topology(out, levels, adj=A48) == oracle.level_topology(img, levels, adj=A48)
+    # the two adjacency pairs are different operators on this image
+    assert not np.array_equal(out, oracle.thin(img, lam)[0])
