@@ -8,6 +8,16 @@ region.  Timing: CUDA events on the launching stream around each step,
 barrier + synchronize around the K timed steps, max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload large|uneven|serve   (the other configurations)
+
+--workload large: 4096x4096 u8 and 8192x8192 u16 (values 0..4095) at lambda
+0 and 30 on the tiled engine, with a halo sweep; reports Gpix-sweeps/s and
+the HBM roofline.  --workload uneven: 1024 u8 images with sides log-uniform
+in [64, 2048] and lambda in {0, 10, 25}, one thin_batch call against one
+thin_run call per image.  --workload serve: Poisson arrivals of u8/u16 images
+with sides log-uniform in [128, 4096] through the serving API under a 40 GB
+budget, against a plain one-image-at-a-time path; p50/p99 latency and
+images/s per arrival rate.
 
 --impl reference times the CPU oracle (the plain sequential subfield
 schedule) on this host's cores over a bounded sample of the same jobs.
@@ -334,6 +344,315 @@ def run_reference(args, rank: int, world: int):
     }
 
 
+# ------------------------------------------------------------------ other configurations
+
+def _gen_pool(specs, workers):
+    """Generates images for (h, w, dtype, seed[, vmax]) specs in a spawn pool (before any device work)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, workers)) as pool:
+        return pool.map(_gen_one, specs, chunksize=1)
+
+
+def _gen_one(spec):
+    from paper_1603_09180_gb300.synth import value_noise_image
+    h, w, dt, seed = spec[:4]
+    vmax = spec[4] if len(spec) > 4 else None
+    return value_noise_image(h, w, dt, seed=seed, vmax=vmax)
+
+
+def _to_dev(a, dev):
+    import numpy as np
+    import torch
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).to(dev).view(torch.uint16)
+    return torch.from_numpy(a).to(dev)
+
+
+def _peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _timed(fn, restore, flush, stream, steps, warmup):
+    """CUDA-event times (ms) of `steps` calls of fn, each after restore() and an L2 flush."""
+    import torch
+    for _ in range(warmup):
+        restore()
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        restore()
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def run_large(args):
+    """Large single images on the tiled engine (temporal blocking, active tiles)."""
+    import torch
+    from paper_1603_09180_gb300 import thin
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    thin.load()
+    cases = [(4096, 4096, "u8", 255, (0, 30)), (8192, 8192, "u16", 4095, (0, 30))]
+    imgs = _gen_pool([(h, w, dt, 1603 + i, vmax) for i, (h, w, dt, vmax, _) in enumerate(cases)], 2)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, src = _peak_hbm()
+    results = []
+    with ClockSampler(0) as clk:
+        for (h, w, dt, vmax, lams), img in zip(cases, imgs):
+            pristine = _to_dev(img, dev)
+            work = pristine.clone()
+            es = work.element_size()
+            for lam in lams:
+                work.copy_(pristine)
+                st = thin.run(work, lam, kernel="tiled")
+                tw, th, H = 64, 32, 8
+                ms = _timed(lambda: thin.run(work, lam, kernel="tiled", stats=False), lambda: work.copy_(pristine),
+                            flush, stream, args.steps, args.warmup)
+                t = statistics.median(ms) / 1e3
+                active = st["tiles_visited"] * tw * th * H / 4.0  # pixel-rounds over active tiles
+                full = w * h * st["phases"] / 4.0
+                results.append({
+                    "image": "%dx%d %s" % (w, h, dt), "lambda": lam, "ms": round(t * 1e3, 3), "phases": st["phases"],
+                    "tiles_visited": st["tiles_visited"], "tested": st["tested"],
+                    "gpix_sweeps_per_s": round(active / t / 1e9, 2),
+                    "gpix_sweeps_full_per_s": round(full / t / 1e9, 2),
+                    "point_tests_per_s_g": round(st["tested"] / t / 1e9, 2),
+                    "achieved_gbs": round(2 * es * active / t / 1e9, 1),
+                    "frac": round(2 * es * active / t / 1e9 / peak, 4)})
+            if dt == "u8":  # halo sweep on 4096^2 u8, lambda 30
+                sweep = {}
+                for H in (3, 4, 5, 6, 7, 8):
+                    ms = _timed(lambda: thin.run(work, 30, kernel="tiled", halo=H, stats=False),
+                                lambda: work.copy_(pristine), flush, stream, 1, 1)
+                    sweep[H] = round(ms[0], 3)
+                results[-1]["halo_sweep_ms"] = sweep
+            del pristine, work
+            torch.cuda.empty_cache()
+    head = results[1]
+    return {"metric": "Gpix-sweeps/s (4096^2 u8, lambda 30, active tiles)", "value": head["gpix_sweeps_per_s"],
+            "unit": "Gpix-sweeps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u8/u16", "data": "synthetic", "workload": "large",
+            "config": {"workload": "4096x4096 u8 and 8192x8192 u16 (0..4095), lambda 0 and 30, tiled engine "
+                                   "64x32 tiles, halo 8", "l2": "flushed before every timed run"},
+            "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": head["frac"], "peak_source": src,
+                         "note": "2 B (u8) or 4 B (u16) per pixel-round over active tiles"},
+            "cases": results, "clocks": clk.summary()}
+
+
+def run_uneven(args):
+    """1024 uneven u8 images: one thin_batch call against one thin_run per image."""
+    import numpy as np
+    import torch
+    from paper_1603_09180_gb300 import synth, thin
+    specs = synth.uneven_batch_specs(args.uneven_n)
+    imgs = _gen_pool([(h, w, "u8", seed) for h, w, lam, seed in specs], host_cores())
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    thin.load()
+    lams = [lam for _, _, lam, _ in specs]
+    pristine = [_to_dev(a, dev) for a in imgs]
+    work = [p.clone() for p in pristine]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        for a, b in zip(work, pristine):
+            a.copy_(b)
+
+    plan = thin.BatchPlan(work, lams)
+    restore()
+    sts, rc = plan.run(stream, stats=True)
+    assert rc == 0, rc
+    batch_out = [t.clone() for t in work]
+    gplan = thin.GraphPlan(work, lams)
+    with ClockSampler(0) as clk:
+        ms_batch = _timed(lambda: plan.run(stream), restore, flush, stream, args.steps, args.warmup)
+        ms_graph = _timed(lambda: gplan.run(stream), restore, flush, stream, args.steps, args.warmup)
+        same_graph = all(torch.equal(a, b) for a, b in zip(work, batch_out))
+
+        def per_image():
+            for t, lam in zip(work, lams):
+                thin.run(t, lam, stats=False)
+        restore()
+        per_image()
+        same = all(torch.equal(a, b) for a, b in zip(work, batch_out))
+        ms_single = _timed(per_image, restore, flush, stream, max(1, args.steps // 2), 1)
+    n = len(specs)
+    px = sum(h * w for h, w, _, _ in specs)
+    tb, ts = statistics.median(ms_batch) / 1e3, statistics.median(ms_single) / 1e3
+    return {"metric": "images/s, uneven batch of %d u8 images (sides 64..2048)" % n, "value": round(n / tb, 1),
+            "unit": "images/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic", "workload": "uneven",
+            "config": {"workload": "%d u8 images, w and h log-uniform in [64, 2048], lambda in {0, 10, 25}" % n,
+                       "megapixels": round(px / 1e6, 1), "l2": "flushed before every timed run"},
+            "batch_ms": round(tb * 1e3, 2), "graph_plan_ms": round(statistics.median(ms_graph), 2),
+            "graph_results_equal": same_graph, "per_image_launch_ms": round(ts * 1e3, 2),
+            "per_image_images_per_s": round(n / ts, 1), "speedup_vs_per_image": round(ts / tb, 2),
+            "results_equal": same, "max_phases": max(s["phases"] for s in sts),
+            "mpix_per_s": round(px / tb / 1e6, 1), "clocks": clk.summary()}
+
+
+def run_serve(args):
+    """Poisson arrivals through thin_serve_* against a plain one-image-at-a-time path."""
+    import queue
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_1603_09180_gb300 import synth, thin
+    pool_n = args.serve_pool
+    _, spec0 = synth.serve_trace(1000.0, pool_n)
+    pool = _gen_pool([(h, w, dt, seed) for h, w, dt, lam, seed in spec0], host_cores())
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    thin.load()
+    budget = 40 << 30
+    rates = [float(r) for r in args.serve_rates.split(",")]
+
+    def drive(rate, submit, drain):
+        t_arr, spec = synth.serve_trace(rate, int(rate * args.serve_seconds) + 1, seed=int(rate))
+        sub_t, lat, rejected = {}, [], 0
+        t0 = time.perf_counter()
+        for k, ta in enumerate(t_arr):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            img = pool[k % pool_n]
+            lam = spec[k][3] * (16 if img.dtype == np.uint16 else 1)
+            ts = time.perf_counter()
+            tk = submit(img, lam)
+            if tk is None:
+                rejected += 1
+            else:
+                sub_t[tk] = ts
+        t_sub_end = time.perf_counter()
+        done_t = drain(len(sub_t))
+        for tk, td in done_t.items():
+            lat.append(td - sub_t[tk])
+        t_end = max(done_t.values()) if done_t else t_sub_end
+        lat.sort()
+        pct = lambda q: round(1e3 * lat[min(len(lat) - 1, int(q * len(lat)))], 2) if lat else None
+        return {"rate_per_s": rate, "offered": len(t_arr), "completed": len(lat), "rejected": rejected,
+                "images_per_s": round(len(lat) / (t_end - t0), 1), "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                "submit_s": round(t_sub_end - t0, 2)}
+
+    out = {"served": [], "plain": []}
+    with ClockSampler(0) as clk:
+        for rate in rates:
+            srv = thin.Server(budget, max_slots=args.serve_slots, queue_cap=args.serve_queue)
+            done_t, errors = {}, []
+            lock = threading.Lock()
+
+            def submit(img, lam):
+                try:
+                    return srv.submit(img, lam)
+                except thin.ThinError as e:
+                    if e.code == thin.THIN_EAGAIN:
+                        return None
+                    raise
+
+            def collector(stop):
+                while True:
+                    t = srv.wait_any(50)
+                    if t is None:
+                        if stop.is_set():
+                            return
+                        continue
+                    td = time.perf_counter()
+                    ok, res, st, rc = srv.poll(t)
+                    with lock:
+                        if ok and rc == 0:
+                            done_t[t] = td
+                        else:
+                            errors.append(rc)
+
+            stop = threading.Event()
+            col = threading.Thread(target=collector, args=(stop,), daemon=True)
+            col.start()
+
+            def drain(n):
+                t_lim = time.perf_counter() + 60
+                while time.perf_counter() < t_lim:
+                    with lock:
+                        if len(done_t) + len(errors) >= n:
+                            break
+                    time.sleep(0.002)
+                stop.set()
+                col.join()
+                return dict(done_t)
+
+            r = drive(rate, submit, drain)
+            r["errors"] = len(errors)
+            out["served"].append(r)
+            print("served", json.dumps(r), file=sys.stderr, flush=True)
+            srv.close()
+
+            # plain path: one worker, one image at a time (H2D, thin_run, D2H), same queue cap
+            q = queue.Queue(maxsize=args.serve_queue)
+            done_p, errors_p = {}, []
+            nxt = [0]
+
+            def worker():
+                while True:
+                    item = q.get()
+                    if item is None:
+                        return
+                    tk, img, lam = item
+                    try:
+                        t = _to_dev(img, dev)
+                        thin.run(t, lam, stats=False)
+                        t.cpu()
+                        done_p[tk] = time.perf_counter()
+                    except Exception:
+                        errors_p.append(tk)
+
+            wt = threading.Thread(target=worker, daemon=True)
+            wt.start()
+
+            def submit_p(img, lam):
+                nxt[0] += 1
+                try:
+                    q.put_nowait((nxt[0], img, lam))
+                    return nxt[0]
+                except queue.Full:
+                    return None
+
+            def drain_p(n):
+                t_lim = time.perf_counter() + 60
+                while len(done_p) + len(errors_p) < n and time.perf_counter() < t_lim:
+                    time.sleep(0.002)
+                q.put(None)
+                wt.join(timeout=5)
+                return dict(done_p)
+
+            r = drive(rate, submit_p, drain_p)
+            r["errors"] = len(errors_p)
+            out["plain"].append(r)
+            print("plain", json.dumps(r), file=sys.stderr, flush=True)
+    head = out["served"][0]
+    return {"metric": "served images/s and p99 latency (Poisson arrivals)", "value": head["images_per_s"],
+            "unit": "images/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u8/u16", "data": "synthetic",
+            "workload": "serve",
+            "config": {"workload": "Poisson arrivals, sides log-uniform [128, 4096], u8/u16 1:1, lambda {0, 10} "
+                                   "(x16 for u16), %d-image pool cycled" % pool_n, "budget_bytes": budget,
+                       "max_slots": args.serve_slots, "queue_cap": args.serve_queue,
+                       "seconds_per_rate": args.serve_seconds},
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "rates": out, "clocks": clk.summary()}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +664,13 @@ def main(argv=None):
     ap.add_argument("--halo", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per batch (profiling runs use fewer)")
+    ap.add_argument("--workload", default="batch192", choices=["batch192", "large", "uneven", "serve"])
+    ap.add_argument("--uneven-n", type=int, default=1024)
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-queue", type=int, default=256)
     args = ap.parse_args(argv)
     globals()["N_IMAGES"] = args.images
     if args.warmup < 3 and args.impl == "native":
@@ -353,7 +679,9 @@ def main(argv=None):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.workload != "batch192" and args.impl == "native":
+        line = {"large": run_large, "uneven": run_uneven, "serve": run_serve}[args.workload](args) if rank == 0 else None
+    elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
         if world > 1:

@@ -1,7 +1,8 @@
 /*
  * thin.h -- C-ABI of the GB300 grayscale lambda-thinning library (libthin.so).
  *
- * The operation: grayscale lambda-thinning under (8,4)-adjacency.  Every
+ * The operation: grayscale lambda-thinning under (8,4)- or (4,8)-adjacency
+ * (Sec. 2.1: n for the sections of F, nbar for their complements).  Every
  * lambda-destructible point (Sec. 2.1: a destructible point, or a
  * k-divergent point with at least k-1 lower components c such that
  * F(x) - F^-(c) <= lambda) is lowered to alpha^-(x, F), the largest value among
@@ -45,7 +46,7 @@ extern "C" {
 
 #define THIN_OK 0
 #define THIN_ERR_ARG (-1)           /* bad pointer, size, pitch, dtype, lambda or option */
-#define THIN_ERR_UNSUPPORTED (-2)   /* (4,8)-adjacency, or an option this build lacks */
+#define THIN_ERR_UNSUPPORTED (-2)   /* an option this build lacks */
 #define THIN_ERR_OOM (-3)           /* scratch allocation failed */
 #define THIN_ERR_NOT_CONVERGED (-4) /* stopped by max_phases before stability */
 #define THIN_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
@@ -54,12 +55,24 @@ extern "C" {
 #define THIN_ERR_TOO_LARGE (-8)     /* thin_run_noalloc: the image needs more than its fixed scratch */
 
 typedef enum { THIN_U8 = 0, THIN_U16 = 1 } thin_dtype;
+/* Adjacency pair (n, nbar) of Sec. 2.1: (8,4) or (4,8).  Under (4,8), T+
+ * counts 4-components of Gamma^+ that hold a 4-neighbour of x, T-- counts
+ * 8-components of Gamma^--, and an end point has one 4-neighbour in F_k. */
 typedef enum { THIN_ADJ_8_4 = 0, THIN_ADJ_4_8 = 1 } thin_adj;
 
 /* Reading of F^-(c) in the lambda rule (Sec. 2.1 leaves F^- undefined):
  * THIN_RULE_MAX takes the largest value of F over the component c (default),
  * THIN_RULE_MIN the smallest. */
 typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
+
+/* The operator (Sec. 2.1-2.2), both lowering points to alpha^-(x, F) in the
+ * same subfield schedule:
+ * THIN_OP_THINNING  lambda-thinning: lower lambda-destructible points (default);
+ * THIN_OP_SKELETON  lambda-skeleton, the paper's operator: lower points that
+ *                   are lambda-deletable (lambda-destructible, or a peak point,
+ *                   T+ = 0, with F(x) - alpha^- <= lambda) and not lambda-end
+ *                   (an end point of F_k, k = F(x), with F(x) - alpha^- > lambda). */
+typedef enum { THIN_OP_THINNING = 0, THIN_OP_SKELETON = 1 } thin_op;
 
 /* Kernel family.  RESIDENT holds each image in the shared memory of one
  * thread-block cluster (images up to about 1.7 MB); TILED streams 64 x 32
@@ -82,6 +95,8 @@ typedef struct {
     int32_t reserved;
     int64_t start_phase; /* global phase index of the first phase (resume), >= 0 */
     int64_t max_phases;  /* stop after this many phases; < 0 = run to stability */
+    int32_t op;          /* thin_op */
+    int32_t reserved2;
 } thin_options;
 
 typedef struct {
@@ -98,7 +113,7 @@ typedef struct {
                                   four phases); the work behind the sweep rate */
 } thin_stats;
 
-/* Fills *opt with the defaults (rule MAX, AUTO kernel, default tiles, phase 0, no cap). */
+/* Fills *opt with the defaults (rule MAX, AUTO kernel, default tiles, phase 0, no cap, lambda-thinning). */
 void thin_default_options(thin_options *opt);
 
 /*
@@ -111,7 +126,7 @@ void thin_default_options(thin_options *opt);
  *   pitch_bytes  distance between rows, >= w * element size
  *   dt           THIN_U8 or THIN_U16
  *   lambda       the contrast parameter, an integer >= 0 (Sec. 2.1)
- *   adj          THIN_ADJ_8_4; THIN_ADJ_4_8 returns THIN_ERR_UNSUPPORTED
+ *   adj          THIN_ADJ_8_4 or THIN_ADJ_4_8
  *   stream       cudaStream_t as void*
  *   opt          options, NULL = defaults
  *   out          stats, NULL = fully asynchronous call
@@ -138,6 +153,53 @@ typedef struct {
 int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const thin_options *opt,
                thin_stats *out);
 
+/* ----------------------------------------------------------------------
+ * Batch plans: thin_batch prepared once and run many times as one CUDA graph
+ * (the graph-captured form of the batch drive; the paper has no counterpart,
+ * its drive is the CPU FIFO of Sec. 3.2).
+ *
+ * thin_plan_create does all host work of a thin_batch call once (checks,
+ * launch groups, device job tables, tensor maps) and captures the device
+ * work of one run into a CUDA graph: per-run resets, the resident engine's
+ * launch groups side by side, the tiled engine after them.
+ * thin_plan_launch enqueues that graph: every image is thinned in place, with
+ * exactly the result thin_batch gives.  The images must stay at the same
+ * device addresses while the plan exists; relaunching thins whatever the
+ * images hold then (restore them first to repeat a run).  Launches of one
+ * plan must not overlap on the device (they share the plan's tables).
+ * -------------------------------------------------------------------- */
+typedef struct thin_plan thin_plan;
+
+/* jobs, n, adj, opt as for thin_batch (the NAIVE kernel returns
+ * THIN_ERR_UNSUPPORTED).  The plan owns device memory (cudaMalloc) until it
+ * is destroyed.  Synchronous: returns once the plan is ready. */
+int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_options *opt, thin_plan **out);
+
+/* Enqueues one run on stream (asynchronous). */
+int thin_plan_launch(thin_plan *p, void *stream);
+
+/* Waits for stream and writes the stats of the plan's last run, one per job
+ * (n entries).  Returns THIN_OK or the first non-OK status, as thin_batch. */
+int thin_plan_stats(thin_plan *p, void *stream, thin_stats *out);
+
+/* Waits for the device to be idle, then frees the plan. */
+int thin_plan_destroy(thin_plan *p);
+
+/*
+ * Autotuner of the tiled engine (temporal blocking, Sec. 2.2's lowering loop
+ * run h phases per tile visit; the paper has no counterpart).  Times every
+ * candidate tile shape and halo depth h (phases per visit) on a scratch copy
+ * of the image -- the image itself is not changed -- and writes the fastest
+ * into opt->tile_w, opt->tile_h and opt->halo (other fields of *opt are kept
+ * and used for the trials: rule, start_phase).  trial_phases bounds each
+ * trial (< 0: every trial runs to stability).  best_ms (may be NULL)
+ * receives the winner's time.  Synchronous.  Candidates: 64x32 (h 8, 6, 4),
+ * 128x32, 64x64, 128x64, 32x32, 96x48, 128x16, 224x32, 48x64 (h 8), 64x16
+ * (h 6).  THIN_ERR_ARG for an image without interior points.
+ */
+int thin_autotune(const void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
+                  void *stream, int64_t trial_phases, thin_options *opt, float *best_ms);
+
 /*
  * The 256-entry point-test table the kernels use, written to out[256]
  * (host memory, no GPU needed).  Entry m describes a point whose strictly
@@ -152,6 +214,10 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
  *   bit 31     k-divergent (T-- >= 2)
  */
 void thin_point_table(uint32_t out[256]);
+
+/* The same table for either adjacency pair; thin_point_table is
+ * thin_point_table_adj(THIN_ADJ_8_4, out). */
+void thin_point_table_adj(thin_adj adj, uint32_t out[256]);
 
 /*
  * thin_run_noalloc: thin_run with the tiled engine for callers that cannot
@@ -187,31 +253,62 @@ int thin_run_noalloc(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype
 const char *thin_version(void);
 
 /* ----------------------------------------------------------------------
- * Serving: continuous batching under a device-memory budget.
- * A server owns a worker thread and a CUDA stream.  submit copies the host
- * image into a device slot and returns at once with a ticket; the worker
- * admits queued requests while the slots and the byte budget allow, runs the
- * active set with the batch engine, and retires each image as soon as it is
- * stable; poll copies a finished image back to the host.
+ * Serving: continuous batching under a device-memory budget (the batch and
+ * serve drive of the GPU form; the paper's own drive is the FIFO of Sec. 3.2,
+ * run by CPU threads).
+ *
+ * A server owns four worker lanes (host threads, each with its own CUDA
+ * stream) on the device that is current at thin_serve_create.  submit copies
+ * the host image into a pinned host buffer and returns at once with a ticket.
+ * An idle lane admits queued requests in arrival order while the slot count
+ * and the byte budget allow (a request that does not fit waits at the head of
+ * the queue), allocates their device images, copies them in, thins them with
+ * one thin_batch call, copies the results back and retires them, returning
+ * their bytes and slots.  Host staging is one pinned arena allocated at
+ * create (a quarter of the device budget, clamped to 256 MiB .. 4 GiB), so
+ * submit makes no CUDA allocation.  Requests that arrive while other batches run are
+ * admitted by the next idle lane and run on the device beside them.  Each
+ * image gets exactly the result thin_run gives it alone (rule MAX, default
+ * options, (8,4)-adjacency).  The server's functions may be called from any
+ * host threads.
  * -------------------------------------------------------------------- */
 typedef struct thin_server thin_server;
 
-/* device_budget_bytes: cap on device bytes held by admitted requests (image
- * plus scratch); max_slots: cap on requests in flight; queue_cap: cap on
- * requests waiting for admission (submit returns THIN_EAGAIN beyond it). */
+/* device_budget_bytes: cap on the device bytes charged by admitted requests;
+ * a request is charged twice its image (16-byte aligned rows) plus 1/4 byte
+ * a pixel plus 64 KiB, which covers the engines' scratch.  max_slots: cap on
+ * requests admitted at once.  queue_cap: cap on requests waiting for
+ * admission.  Returns THIN_ERR_ARG for a zero budget or cap, THIN_ERR_CUDA
+ * if no device is usable, THIN_ERR_OOM if the pinned staging arena cannot be
+ * allocated. */
 int thin_serve_create(size_t device_budget_bytes, int max_slots, int queue_cap, thin_server **out);
 
-/* Queue one host image (copied before return).  *ticket identifies it. */
+/* Queue one host image (any host memory: it is copied before the call
+ * returns; rows pitch bytes apart).  *ticket identifies it.  Returns
+ * THIN_EAGAIN when queue_cap requests are already waiting or the pinned
+ * staging arena is full (nothing queued; try again later),
+ * THIN_ERR_TOO_LARGE when the image alone is charged more than the budget or
+ * is larger than the staging arena.
+ * Images narrower or lower than 3 pixels finish at once, unchanged. */
 int thin_serve_submit(thin_server *s, const void *host_img, int w, int h, size_t pitch,
                       thin_dtype dt, uint32_t lambda, uint64_t *ticket);
 
-/* Non-blocking: *done = 1 and the result copied to host_out (out_pitch bytes
- * per row) once the request is finished; the ticket is then retired.
- * *done = 0 while it is queued or running.  stats may be NULL. */
+/* Non-blocking: *done = 0 while the request is queued or running.  Once it
+ * has finished, *done = 1, the result is copied to host_out (rows out_pitch
+ * bytes apart), stats (may be NULL) are filled and the ticket is retired; the
+ * return value is then the request's status (THIN_OK, or the error its batch
+ * met).  An unknown or retired ticket returns THIN_ERR_ARG. */
 int thin_serve_poll(thin_server *s, uint64_t ticket, void *host_out, size_t out_pitch, int *done,
                     thin_stats *stats);
 
-/* Stops the worker (finishing admitted work) and frees everything. */
+/* Blocks up to timeout_ms for a finished request that has not been polled
+ * yet and stores its ticket (finished requests come out in the order they
+ * finished).  Returns THIN_EAGAIN on timeout.  The server remembers the last
+ * 4 x (max_slots + queue_cap) finishes only. */
+int thin_serve_wait_any(thin_server *s, int timeout_ms, uint64_t *ticket);
+
+/* Stops the lanes (each finishes the batch it admitted; requests still
+ * waiting for admission are dropped) and frees everything, tickets included. */
 int thin_serve_destroy(thin_server *s);
 
 #ifdef __cplusplus

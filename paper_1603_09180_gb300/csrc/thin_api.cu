@@ -17,11 +17,24 @@ int cuda_status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? THIN_ERR_OOM : THIN_ERR_CUDA;
 }
 
+cudaError_t allow_max_dynamic_smem(const void *kernel)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);  // static shared memory counts against the cap
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+    return e;
+}
+
 namespace {
 
 int check_options(const thin_options &o)
 {
     if (o.rule != THIN_RULE_MAX && o.rule != THIN_RULE_MIN) return THIN_ERR_ARG;
+    if (o.op != THIN_OP_THINNING && o.op != THIN_OP_SKELETON) return THIN_ERR_ARG;
     if (o.kernel < THIN_KERNEL_AUTO || o.kernel > THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;
     if (o.start_phase < 0) return THIN_ERR_ARG;
     if (o.tile_w < 0 || o.tile_h < 0 || o.halo < 0) return THIN_ERR_ARG;
@@ -42,62 +55,184 @@ int check_image(const void *img, int w, int h, size_t pitch, int dt)
     return 0;
 }
 
-// Runs images on the resident engine where they fit (AUTO, RESIDENT) and on
-// the tiled engine otherwise; stats land at the images' own positions.
-int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out)
+}  // namespace
+
+// Splits validated images into launch groups: images that fit the shared
+// memory of a cluster go to the resident engine, grouped by cluster size
+// (AUTO, RESIDENT); the rest go to the tiled engine (AUTO, TILED).  When few
+// images fit, each is spread over a wider cluster (at least 32 rows a block)
+// so that more SMs work on it.
+int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G)
 {
     const int n = int(specs.size());
-    const int nw = 16;  // warps per resident block (one block per SM measured fastest)
+    G->resident.clear();
+    G->tiled.clear();
+    G->nw = 16;  // warps per resident block (one block per SM measured fastest)
     std::vector<int> cls(n, 0);
     if (o.kernel == THIN_KERNEL_AUTO || o.kernel == THIN_KERNEL_RESIDENT) {
-        const size_t limit = resident_smem_limit(16 / nw);
+        const size_t limit = resident_smem_limit(16 / G->nw);
         for (int k = 0; k < n; ++k)
-            cls[k] = resident_cluster_size(specs[k].w, specs[k].h, specs[k].dtype, limit, nw, nullptr, nullptr);
+            cls[k] = resident_cluster_size(specs[k].w, specs[k].h, specs[k].dtype, limit, G->nw, nullptr, nullptr);
     }
     int eligible = 0, sms = 0, dev = 0;
     for (int k = 0; k < n; ++k) eligible += cls[k] > 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // few images: spread each over more blocks of a wider cluster
     int spread = 1;
-    while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms * (16 / nw)) spread *= 2;
-    int rc = THIN_OK;
+    while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms * (16 / G->nw)) spread *= 2;
     for (int C = 1; C <= 8; C *= 2) {
-        std::vector<JobSpec> group;
-        std::vector<int> where;
+        std::vector<int> idx;
         for (int k = 0; k < n; ++k) {
             if (cls[k] <= 0) continue;
-            int c = cls[k];  // spread, but keep at least 32 rows per block
+            int c = cls[k];
             while (c < spread && specs[k].h / (2 * c) >= 32) c *= 2;
-            if (c == C) {
-                group.push_back(specs[k]);
-                where.push_back(k);
-            }
+            if (c == C) idx.push_back(k);
         }
-        if (group.empty()) continue;
-        std::vector<thin_stats> st(out ? group.size() : 0);
-        const int r = resident_run(group.data(), int(group.size()), C, nw, o, s, out ? st.data() : nullptr);
-        if (out)
-            for (size_t k = 0; k < group.size(); ++k) out[where[k]] = st[k];
-        if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;
-        if (r != THIN_OK && rc == THIN_OK) rc = r;
+        if (!idx.empty()) G->resident.push_back({C, idx});
     }
-    std::vector<JobSpec> rest;
-    std::vector<int> where;
     for (int k = 0; k < n; ++k)
-        if (cls[k] == 0) {
-            rest.push_back(specs[k]);
-            where.push_back(k);
-        }
-    if (!rest.empty()) {
-        if (o.kernel == THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;  // does not fit on chip
-        std::vector<thin_stats> st(out ? rest.size() : 0);
-        const int r = tiled_run(rest.data(), int(rest.size()), o, s, out ? st.data() : nullptr);
-        if (out)
-            for (size_t k = 0; k < rest.size(); ++k) out[where[k]] = st[k];
-        if (r != THIN_OK && r != THIN_ERR_NOT_CONVERGED) return r;
-        if (r != THIN_OK && rc == THIN_OK) rc = r;
+        if (cls[k] == 0) G->tiled.push_back(k);
+    if (!G->tiled.empty() && o.kernel == THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;  // does not fit on chip
+    return THIN_OK;
+}
+
+namespace {
+
+// Helper streams of the calling host thread for running launch groups side
+// by side (created once per thread and device, kept until the process exits).
+struct SideStreams {
+    int dev = -1;
+    cudaStream_t s[5] = {};
+    cudaEvent_t ev[6] = {};
+};
+
+cudaError_t side_streams(SideStreams **out)
+{
+    thread_local SideStreams t;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (t.dev != dev) {
+        SideStreams n;
+        n.dev = dev;
+        for (auto &x : n.s)
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        for (auto &x : n.ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        t = n;
     }
+    *out = &t;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, const thin_options &o,
+                       cudaStream_t s, bool async_alloc)
+{
+    specs = specs_in;
+    opt = o;
+    async = async_alloc;
+    for (const auto &grp : G.resident) {
+        std::vector<JobSpec> js;
+        for (int k : grp.second) js.push_back(specs[k]);
+        res.emplace_back();
+        res_idx.push_back(grp.second);
+        const int rc = resident_prepare(js.data(), int(js.size()), grp.first, G.nw, o, s, async_alloc, &res.back());
+        if (rc != THIN_OK) return rc;
+    }
+    if (!G.tiled.empty()) {
+        std::vector<JobSpec> js;
+        for (int k : G.tiled) js.push_back(specs[k]);
+        tiled_idx = G.tiled;
+        const int rc = tiled_prepare(js.data(), int(js.size()), o, s, async_alloc, &tiled);
+        if (rc != THIN_OK) return rc;
+    }
+    return THIN_OK;
+}
+
+// Resident groups run side by side on helper streams forked from s (a
+// group's clusters take SMs as another group's finish); the tiled group,
+// whose grid barrier needs all its blocks resident at once, runs after them
+// on s.
+cudaError_t Execution::enqueue(cudaStream_t s, cudaStream_t *side, cudaEvent_t *ev) const
+{
+    cudaError_t e = cudaSuccess;
+    const int ng = int(res.size());
+    if (ng == 1) {
+        e = resident_enqueue(res[0], s);
+    } else if (ng > 1) {
+        e = cudaEventRecord(ev[0], s);
+        for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+            e = cudaStreamWaitEvent(side[g], ev[0], 0);
+            if (e == cudaSuccess) e = resident_enqueue(res[g], side[g]);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + g], side[g]);
+        }
+        for (int g = 0; g < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(s, ev[1 + g], 0);
+    }
+    if (e == cudaSuccess && tiled) e = tiled_enqueue(tiled, s);
+    return e;
+}
+
+int Execution::collect(cudaStream_t s, thin_stats *out) const
+{
+    int rc = THIN_OK;
+    for (size_t g = 0; g < res.size(); ++g) {
+        std::vector<thin_stats> st(res_idx[g].size());
+        const int r = resident_collect(res[g], opt, s, st.data());
+        for (size_t k = 0; k < st.size(); ++k) out[res_idx[g][k]] = st[k];
+        if (r != THIN_OK && (rc == THIN_OK || rc == THIN_ERR_NOT_CONVERGED)) rc = r;
+    }
+    if (tiled) {
+        std::vector<thin_stats> st(tiled_idx.size());
+        const int r = tiled_collect(tiled, opt, s, st.data());
+        for (size_t k = 0; k < st.size(); ++k) out[tiled_idx[k]] = st[k];
+        if (r != THIN_OK && (rc == THIN_OK || rc == THIN_ERR_NOT_CONVERGED)) rc = r;
+    }
+    return rc;
+}
+
+void Execution::release(cudaStream_t s)
+{
+    for (auto &r : res) resident_release(r, s);
+    res.clear();
+    if (tiled) tiled_release(tiled, s);
+    tiled = nullptr;
+}
+
+namespace {
+
+// Runs validated images in one device-driven pass: every launch group
+// prepared, enqueued side by side, stats collected if asked for.
+int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out)
+{
+    if (o.max_phases == 0) {  // nothing may run: every image stays as it is, unconverged
+        if (out)
+            for (size_t k = 0; k < specs.size(); ++k) {
+                std::memset(&out[k], 0, sizeof out[k]);
+                out[k].status = THIN_ERR_NOT_CONVERGED;
+                out[k].last_change_phase = -1;
+                out[k].end_phase = o.start_phase;
+            }
+        return THIN_ERR_NOT_CONVERGED;
+    }
+    Grouping G;
+    int rc = group_jobs(specs, o, &G);
+    if (rc != THIN_OK) return rc;
+    SideStreams *ss = nullptr;
+    if (G.resident.size() > 1) {
+        const cudaError_t e = side_streams(&ss);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    Execution X;
+    rc = X.prepare(specs, G, o, s, true);
+    if (rc == THIN_OK) {
+        const cudaError_t e = X.enqueue(s, ss ? ss->s : nullptr, ss ? ss->ev : nullptr);
+        if (e != cudaSuccess) rc = cuda_status(e);
+        else if (out) rc = X.collect(s, out);
+    }
+    X.release(s);
     return rc;
 }
 
@@ -134,14 +269,19 @@ void thin_point_table(uint32_t out[256])
     for (int i = 0; i < 256; ++i) out[i] = kPointTable.v[i];
 }
 
+void thin_point_table_adj(thin_adj adj, uint32_t out[256])
+{
+    if (!out) return;
+    for (int i = 0; i < 256; ++i) out[i] = adj == THIN_ADJ_4_8 ? kPointTable48.v[i] : kPointTable.v[i];
+}
+
 int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda, thin_adj adj,
              void *stream, const thin_options *opt, thin_stats *out)
 {
     thin_options o;
     thin_default_options(&o);
     if (opt) o = *opt;
-    if (adj == THIN_ADJ_4_8) return THIN_ERR_UNSUPPORTED;
-    if (adj != THIN_ADJ_8_4) return THIN_ERR_ARG;
+    if (adj != THIN_ADJ_8_4 && adj != THIN_ADJ_4_8) return THIN_ERR_ARG;
     int rc = check_options(o);
     if (rc) return rc;
     rc = check_image(img_dev, w, h, pitch_bytes, dt);
@@ -150,7 +290,7 @@ int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uin
         if (out) noop_stats(o, out);
         return THIN_OK;
     }
-    JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda};
+    JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda, int(adj)};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (o.kernel == THIN_KERNEL_NAIVE) return naive_run(j, o, s, out);
     if (o.kernel == THIN_KERNEL_TILED) return tiled_run(&j, 1, o, s, out);
@@ -163,8 +303,7 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
     thin_default_options(&o);
     if (opt) o = *opt;
     if (n < 0 || (n > 0 && !jobs)) return THIN_ERR_ARG;
-    if (adj == THIN_ADJ_4_8) return THIN_ERR_UNSUPPORTED;
-    if (adj != THIN_ADJ_8_4) return THIN_ERR_ARG;
+    if (adj != THIN_ADJ_8_4 && adj != THIN_ADJ_4_8) return THIN_ERR_ARG;
     int rc = check_options(o);
     if (rc) return rc;
     std::vector<JobSpec> specs;
@@ -178,7 +317,7 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
             if (out) noop_stats(o, &out[k]);
             continue;
         }
-        specs.push_back(JobSpec{J.img_dev, J.w, J.h, J.pitch, J.dtype, J.lambda});
+        specs.push_back(JobSpec{J.img_dev, J.w, J.h, J.pitch, J.dtype, J.lambda, int(adj)});
         where.push_back(k);
     }
     if (specs.empty()) return THIN_OK;

@@ -80,27 +80,77 @@ constexpr uint32_t point_entry(unsigned lower)
     return e;
 }
 
+// Table entry under (4,8)-adjacency (Sec. 2.1 allows both pairs): T+ counts
+// the 4-components of the neighbours >= F(x) that hold a 4-neighbour of x
+// (4-adjacent ring points are cyclically consecutive, so these are runs);
+// T-- counts the 8-components of the lower neighbours (every ring point is
+// 8-adjacent to x), found by union-find over ring 8-adjacency.
+constexpr uint32_t point_entry48(unsigned lower)
+{
+    lower &= 0xffu;
+    const unsigned upper = ~lower & 0xffu;
+    uint32_t tplus = 0;
+    if (upper == 0xffu) {
+        tplus = 1;
+    } else if (upper) {
+        int s = 0;
+        while ((upper >> s) & 1u) ++s;  // a position outside Gamma^+
+        bool run = false, has_four = false;
+        for (int t = 1; t <= 8; ++t) {
+            const int i = (s + t) & 7;
+            if ((upper >> i) & 1u) {
+                run = true;
+                if ((i & 1) == 0) has_four = true;
+            } else {
+                if (run && has_four) ++tplus;
+                run = false;
+                has_four = false;
+            }
+        }
+    }
+    int p[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+    for (int i = 0; i < 8; ++i) {
+        const int j = (i + 1) & 7;
+        if (((lower >> i) & 1u) && ((lower >> j) & 1u)) uf_join(p, i, j);
+        const int k = (i + 2) & 7;
+        if ((i & 1) == 0 && ((lower >> i) & 1u) && ((lower >> k) & 1u)) uf_join(p, i, k);
+    }
+    uint32_t tminus = 0, labels = 0;
+    int label_of_root[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 8; ++i) {
+        if (!((lower >> i) & 1u)) continue;
+        const int r = uf_root(p, i);
+        if (!label_of_root[r]) label_of_root[r] = int(++tminus);
+        labels |= uint32_t(label_of_root[r]) << (3 * i);
+    }
+    uint32_t e = tplus | (tminus << 3) | (labels << kTabLabelShift);
+    if (tplus == 1 && tminus == 1) e |= kTabDestructible;
+    if (tminus >= 2) e |= kTabDivergent;
+    return e;
+}
+
 struct PointTable {
     uint32_t v[256];
 };
 
-constexpr PointTable make_point_table()
+constexpr PointTable make_point_table(int adj)
 {
     PointTable t{};
-    for (unsigned m = 0; m < 256; ++m) t.v[m] = point_entry(m);
+    for (unsigned m = 0; m < 256; ++m) t.v[m] = adj ? point_entry48(m) : point_entry(m);
     return t;
 }
 
-constexpr PointTable kPointTable = make_point_table();
+constexpr PointTable kPointTable = make_point_table(0);
+constexpr PointTable kPointTable48 = make_point_table(1);
 
 // For each lower mask m: byte j holds the ring mask of the j-th counted T--
 // component (the 4-components of Gamma^-- that hold a 4-neighbour of x);
 // unused bytes are 0.  Used by the lambda rule of k-divergent points.
-constexpr PointTable make_component_table()
+constexpr PointTable make_component_table(int adj)
 {
     PointTable t{};
     for (unsigned m = 0; m < 256; ++m) {
-        const uint32_t e = point_entry(m);
+        const uint32_t e = adj ? point_entry48(m) : point_entry(m);
         uint32_t v = 0;
         for (int i = 0; i < 8; ++i) {
             const uint32_t lab = (e >> (kTabLabelShift + 3 * i)) & 7u;
@@ -111,7 +161,13 @@ constexpr PointTable make_component_table()
     return t;
 }
 
-constexpr PointTable kComponentTable = make_component_table();
+constexpr PointTable kComponentTable = make_component_table(0);
+constexpr PointTable kComponentTable48 = make_component_table(1);
+
+// Shared-memory table block of every kernel: point and component tables of
+// (8,4), then of (4,8), 256 words each.
+constexpr int kTabWords = 1024;
+constexpr int kTabOffset48 = 512;
 
 #ifdef __CUDACC__
 
@@ -139,12 +195,20 @@ __device__ __forceinline__ bool divergent_within_lambda(uint32_t e, uint32_t c, 
 }
 
 // The lowering loop of Sec. 2.2 at one point whose neighbours stay fixed:
-// while x is lambda-destructible, F(x) := alpha^-(x, F).  Each step lands on a
-// distinct neighbour value, so at most eight steps succeed.  Returns the new
-// value and adds the number of steps to `nlow`.
+// while x may be lowered, F(x) := alpha^-(x, F).  Each step lands on a
+// distinct neighbour value, so at most eight steps succeed.  `tab` is the
+// point table of the adjacency pair.  mode: bit 0 the F^- reading (0 max,
+// 1 min), bit 1 the operator -- 0: lambda-thinning (x is
+// lambda-destructible), 1: lambda-skeleton (x is lambda-deletable and not
+// lambda-end: lambda-destructible or a peak point, T+ = 0, with
+// F(x) - alpha^- <= lambda; and not an end point, one point of Gamma_n^*(x)
+// >= F(x), with F(x) - alpha^- > lambda); bit 2 the pair, 0: (8,4), 1: (4,8)
+// (n = 4 in the end-point count).  Returns the new value and adds the number
+// of steps to `nlow`.
 __device__ __forceinline__ uint32_t lower_point(uint32_t c, const uint32_t nb[8], const uint32_t *tab,
-                                                uint32_t lam, int rule, int &nlow)
+                                                uint32_t lam, int mode, int &nlow)
 {
+    const int rule = mode & 1;
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
         uint32_t m = 0, alpha = 0;
@@ -158,6 +222,13 @@ __device__ __forceinline__ uint32_t lower_point(uint32_t c, const uint32_t nb[8]
         const uint32_t e = tab[m];
         bool ok = (e & kTabDestructible) != 0;
         if (!ok && (e & kTabDivergent) && lam != 0) ok = divergent_within_lambda(e, c, nb, lam, rule);
+        if (mode & 2) {
+            const bool shallow = c - alpha <= lam;   // F(x) - alpha^- <= lambda
+            const bool peak = (e & 7u) == 0;         // T+ = 0
+            const uint32_t near = (mode & 4) ? 0x55u : 0xffu;  // Gamma_n^*(x): 4- or 8-neighbours
+            const bool end = __popc(~m & near) == 1;  // one of them in F_k, k = F(x)
+            ok = (ok || (peak && shallow)) && !(end && !shallow);
+        }
         if (!ok) break;
         c = alpha;
         ++nlow;

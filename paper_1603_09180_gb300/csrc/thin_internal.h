@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/thin.h"
 
@@ -16,9 +17,15 @@ struct JobSpec {
     size_t pitch;
     int dtype;      // THIN_U8 / THIN_U16
     uint32_t lam;
+    int adj;        // THIN_ADJ_8_4 / THIN_ADJ_4_8
 };
 
 inline int elem_size(int dtype) { return dtype == THIN_U16 ? 2 : 1; }
+
+// The point test's mode word for the kernels: bit 0 the F^- reading
+// (thin_rule), bit 1 the operator (thin_op); the kernels add bit 2, the
+// image's adjacency pair (thin_adj).
+inline int test_mode(const thin_options &o) { return (o.rule & 1) | ((o.op & 1) << 1); }
 
 // Naive engine: one launch per subfield phase over the whole image, in place.
 int naive_run(const JobSpec &job, const thin_options &opt, cudaStream_t stream, thin_stats *out);
@@ -32,15 +39,117 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
 // share an SM) for its whole run.
 int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
                  thin_stats *out);
+// Device-side records of the resident engine (thin_resident.cu).
+struct ResJob {
+    unsigned long long img;    // the caller's image, thinned in place
+    unsigned long long pitch;  // bytes between rows
+    int w, h, dtype;
+    unsigned lam;
+    int rows;   // image rows per block (even)
+    int rp;     // shared row pitch in bytes: 16 B pad | w * es | pad to 16 | 16 B pad
+    int cw;     // cells per row = ceil(w / 8)
+    int wpr;    // bitmap words per cell row = ceil(cw / 32)
+    int bulk;   // rows are 16-byte aligned and a multiple of 16 bytes: stage them by bulk copy
+    int index;  // position of the job in the caller's list
+    int hr;     // halo rows copied from each neighbouring block (even; 0 for a one-block cluster)
+    int steph;  // phases between exchanges of halo rows
+    int adj;    // thin_adj
+    int pad;
+};
+
+struct ResStat {
+    unsigned long long lowered;
+    unsigned long long tested;   // point tests on own rows
+    long long last_change;  // global phase index, -1 if none
+    long long phases;
+    int converged;
+    int error;
+};
+
+struct ResCtl {
+    unsigned next_job;
+    int error;
+    int pad[2];
+};
+
+struct ResArgs {
+    const ResJob *jobs;
+    ResStat *st;
+    ResCtl *ctl;
+    int njobs;
+    int rule;
+    long long start_phase;
+    long long max_phases;
+    unsigned long long timeout_ns;
+};
+
+// A resident launch prepared on the host (device tables uploaded), ready to
+// be enqueued any number of times: see resident_prepare / _enqueue /
+// _collect / _release.
+struct ResidentPrepared {
+    int n = 0, C = 0, nw = 0, grid = 0;
+    size_t smem = 0;
+    bool async_alloc = true;
+    char *base = nullptr;         // one device allocation holding everything below
+    void *st0 = nullptr, *ctl0 = nullptr;  // pristine stats and control words
+    size_t st_bytes = 0;
+    std::vector<int> order;       // launch position -> index in the prepared job list
+    ResArgs P;                    // the kernel's argument block
+};
+int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
+                     bool async_alloc, ResidentPrepared *R);
+cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream);
+int resident_collect(const ResidentPrepared &R, const thin_options &opt, cudaStream_t stream, thin_stats *out);
+void resident_release(ResidentPrepared &R, cudaStream_t stream);
 // Smallest cluster of nw-warp blocks whose shared memory holds a w x h image
 // of `dtype`, 0 if none.
 int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, int *rows_out, int *rp_out);
 // Shared memory one block may take when `blocks` blocks share an SM.
 size_t resident_smem_limit(int blocks);
 
+// A tiled launch prepared on the host (opaque; thin_tiled.cu).
+struct TiledPrepared;
+int tiled_prepare(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, bool async_alloc,
+                  TiledPrepared **out);
+cudaError_t tiled_enqueue(const TiledPrepared *T, cudaStream_t stream);
+int tiled_collect(const TiledPrepared *T, const thin_options &opt, cudaStream_t stream, thin_stats *out);
+void tiled_release(TiledPrepared *T, cudaStream_t stream);
+
 // Defaults of the tiled engine for a dtype (tile width/height in pixels, halo).
 void tiled_defaults(int dtype, int *tw, int *th, int *halo);
 
 int cuda_status(cudaError_t e);
+
+// Launch groups of a batch: (cluster size, job indices) for the resident
+// engine, job indices for the tiled engine.
+struct Grouping {
+    int nw = 16;
+    std::vector<std::pair<int, std::vector<int>>> resident;
+    std::vector<int> tiled;
+};
+int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G);
+
+// Every launch group of a batch, prepared; enqueue() is device work only
+// (resident groups forked onto up to four side streams with events, joined
+// back before the tiled group), so it can be captured in a CUDA graph.
+struct Execution {
+    std::vector<JobSpec> specs;
+    thin_options opt;
+    bool async = true;
+    std::vector<ResidentPrepared> res;
+    std::vector<std::vector<int>> res_idx;
+    TiledPrepared *tiled = nullptr;
+    std::vector<int> tiled_idx;
+    int prepare(const std::vector<JobSpec> &specs, const Grouping &G, const thin_options &o, cudaStream_t s,
+                bool async_alloc);
+    cudaError_t enqueue(cudaStream_t s, cudaStream_t *side, cudaEvent_t *ev) const;
+    int collect(cudaStream_t s, thin_stats *out) const;  // out[k] for specs[k]; waits for s
+    void release(cudaStream_t s);
+};
+
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.
+// Always the same value, so host threads launching the kernel at once with
+// different shared-memory sizes never lower the cap under one another.
+cudaError_t allow_max_dynamic_smem(const void *kernel);
 
 }  // namespace thin

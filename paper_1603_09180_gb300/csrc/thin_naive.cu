@@ -23,13 +23,14 @@ struct NaiveState {
 };
 
 __device__ const PointTable d_naive_table = kPointTable;
+__device__ const PointTable d_naive_table48 = kPointTable48;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_naive_phase(T *img, int w, int h, size_t pitch, int px, int py,
-                                                     uint32_t lam, int rule, long long g, NaiveState *st)
+                                                     uint32_t lam, int mode, long long g, NaiveState *st)
 {
     __shared__ uint32_t tab[256];
-    tab[threadIdx.x] = d_naive_table.v[threadIdx.x];
+    tab[threadIdx.x] = (mode & 4) ? d_naive_table48.v[threadIdx.x] : d_naive_table.v[threadIdx.x];
     __syncthreads();
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + px;
     const int y = 2 * blockIdx.y + py;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) k_naive_phase(T *img, int w, int h, size_
         const T *dn = reinterpret_cast<const T *>(base + size_t(y + 1) * pitch);
         uint32_t nb[8] = {row[x + 1], up[x + 1], up[x], up[x - 1], row[x - 1], dn[x - 1], dn[x], dn[x + 1]};
         const uint32_t c = row[x];
-        const uint32_t c2 = lower_point(c, nb, tab, lam, rule, nl);
+        const uint32_t c2 = lower_point(c, nb, tab, lam, mode, nl);
         if (nl) row[x] = static_cast<T>(c2);
     }
     // one atomic per warp
@@ -79,10 +80,10 @@ int naive_run(const JobSpec &job, const thin_options &opt, cudaStream_t stream, 
             const int p = int(g & 3);
             if (job.dtype == THIN_U8)
                 k_naive_phase<uint8_t><<<grid, block, 0, stream>>>(static_cast<uint8_t *>(job.img), job.w, job.h,
-                                                                   job.pitch, p & 1, p >> 1, job.lam, opt.rule, g, d);
+                                                                   job.pitch, p & 1, p >> 1, job.lam, test_mode(opt) | (job.adj << 2), g, d);
             else
                 k_naive_phase<uint16_t><<<grid, block, 0, stream>>>(static_cast<uint16_t *>(job.img), job.w, job.h,
-                                                                    job.pitch, p & 1, p >> 1, job.lam, opt.rule, g, d);
+                                                                    job.pitch, p & 1, p >> 1, job.lam, test_mode(opt) | (job.adj << 2), g, d);
             ++g;
             ++run;
         }

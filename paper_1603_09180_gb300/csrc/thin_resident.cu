@@ -40,55 +40,16 @@ namespace {
 constexpr int kResMaxWarps = 16;
 constexpr int kResStep = 8;  // phases between halo exchanges = halo rows held from each neighbour
 
-struct ResJob {
-    unsigned long long img;    // the caller's image, thinned in place
-    unsigned long long pitch;  // bytes between rows
-    int w, h, dtype;
-    unsigned lam;
-    int rows;   // image rows per block (even)
-    int rp;     // shared row pitch in bytes: 16 B pad | w * es | pad to 16 | 16 B pad
-    int cw;     // cells per row = ceil(w / 8)
-    int wpr;    // bitmap words per cell row = ceil(cw / 32)
-    int bulk;   // rows are 16-byte aligned and a multiple of 16 bytes: stage them by bulk copy
-    int index;  // position of the job in the caller's list
-    int hr;     // halo rows copied from each neighbouring block (even; 0 for a one-block cluster)
-    int steph;  // phases between exchanges of halo rows
-};
-
-struct ResStat {
-    unsigned long long lowered;
-    unsigned long long tested;   // point tests on own rows
-    long long last_change;  // global phase index, -1 if none
-    long long phases;
-    int converged;
-    int error;
-};
-
-struct ResCtl {
-    unsigned next_job;
-    int error;
-    int pad[2];
-};
-
-struct ResArgs {
-    const ResJob *jobs;
-    ResStat *st;
-    ResCtl *ctl;
-    int njobs;
-    int rule;
-    long long start_phase;
-    long long max_phases;
-    unsigned long long timeout_ns;
-};
-
 __device__ const PointTable d_res_point_table = kPointTable;
 __device__ const PointTable d_res_component_table = kComponentTable;
+__device__ const PointTable d_res_point_table48 = kPointTable48;
+__device__ const PointTable d_res_component_table48 = kComponentTable48;
 
 // Shared-memory map of one block for a job.
-constexpr int kOffTabs = 0;      // point table + component table, 2 KiB
-constexpr int kOffCtrl = 2048;   // control words
-constexpr int kOffBar = 2176;    // mbarrier of the row staging
-constexpr int kOffRows = 2304;   // image rows (16-byte aligned)
+constexpr int kOffTabs = 0;      // point and component tables of (8,4) and (4,8), 4 KiB
+constexpr int kOffCtrl = 4096;   // control words
+constexpr int kOffBar = 4224;    // mbarrier of the row staging
+constexpr int kOffRows = 4352;   // image rows (16-byte aligned)
 
 struct Ctrl {
     int job;
@@ -183,6 +144,8 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
     for (int i = tid; i < 256; i += blockDim.x) {
         tabs[i] = d_res_point_table.v[i];
         tabs[256 + i] = d_res_component_table.v[i];
+        tabs[kTabOffset48 + i] = d_res_point_table48.v[i];
+        tabs[kTabOffset48 + 256 + i] = d_res_component_table48.v[i];
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -199,6 +162,9 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         if (job >= P.njobs) break;
         const ResJob J = P.jobs[job];
         const int es = J.dtype == THIN_U16 ? 2 : 1;
+        const int mode = P.rule | (J.adj << 2);      // F^- reading, operator, adjacency pair
+        const bool simd = es == 1 && J.adj == 0;     // u8 under (8,4): four points at once
+        const uint32_t *ptab = tabs + (J.adj ? kTabOffset48 : 0);
         const int R = J.rows, HR = J.hr, RP = J.rp, CW = J.cw, WPR = J.wpr;
         const int LR = R + 2 * HR;   // shared rows: HR halo rows, R own rows, HR halo rows
         const int CRT = LR / 2;      // cell rows held
@@ -337,7 +303,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                     }
                     __syncwarp();
                     int nl = nq;
-                    if (es == 2 || nq > 32) {
+                    if (!simd || nq > 32) {
                         // test first; the groups that lower are packed to the front of the queue
                         // (in place: a chunk's slots are read before any of them is written)
                         nl = 0;
@@ -352,12 +318,16 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                 where(code, gcr, gcc, vm, in);
                                 ntest += __popc(in);
                                 uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
-                                if (es == 1) {
-                                    lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, P.rule) != 0;
+                                if (simd) {
+                                    lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode) != 0;
                                 } else {
-                                    const uint32_t moved = item_u16(
-                                        reinterpret_cast<const uint16_t *>(rb - RP), reinterpret_cast<uint16_t *>(rb),
-                                        reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in, tabs, J.lam, P.rule, nlow);
+                                    const uint32_t moved =
+                                        es == 2 ? item_table<uint16_t>(reinterpret_cast<const uint16_t *>(rb - RP),
+                                                                       reinterpret_cast<uint16_t *>(rb),
+                                                                       reinterpret_cast<const uint16_t *>(rb + RP), px, vm,
+                                                                       in, ptab, J.lam, mode, nlow)
+                                                : item_table<uint8_t>(rb - RP, rb, rb + RP, px, vm, in, ptab, J.lam, mode,
+                                                                      nlow);
                                     if (moved) {
                                         mark(gcr, gcc, moved);
                                         if (moved & in) moved_own = true;
@@ -369,9 +339,9 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                             nl += __popc(bal);
                         }
                         __syncwarp();
-                        if (es == 2) nl = 0;
+                        if (!simd) nl = 0;
                     }
-                    // lower them (u8); with few groups the loop's first test is the only one
+                    // lower them (u8, (8,4)); with few groups the loop's first test is the only one
                     for (int k = lane; k < nl; k += 32) {
                         const int code = wqueue[k];
                         int gcr, gcc;
@@ -379,7 +349,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                         where(code, gcr, gcc, vm, in);
                         if (nq <= 32) ntest += __popc(in);
                         uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
-                        const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, P.rule, nlow);
+                        const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
                         if (moved) {
                             mark(gcr, gcc, moved);
                             if (moved & in) moved_own = true;
@@ -476,12 +446,12 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
     }
 }
 
-// One launch of k_resident<NW>: as many clusters of C blocks as fit at once
-// (each loops over the job queue), at most one per job.
+// Launch shape of k_resident<NW>: as many clusters of C blocks as fit at
+// once (each loops over the job queue), at most one per job.
 template <int NW>
-cudaError_t resident_launch(int C, int n, size_t smem, cudaStream_t stream, const ResArgs &P)
+cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_resident<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_resident<NW>));
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cudaLaunchAttribute attr[1];
@@ -491,20 +461,33 @@ cudaError_t resident_launch(int C, int n, size_t smem, cudaStream_t stream, cons
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(NW * 32);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
+    cfg.gridDim = dim3(C);
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (e == cudaSuccess) {
-        cfg.gridDim = dim3(C);
-        e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<NW>, &cfg);
-    }
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<NW>, &cfg);
     if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) {
-        cfg.gridDim = dim3(C * std::min(clusters, n));
-        e = cudaLaunchKernelEx(&cfg, k_resident<NW>, P);
-    }
+    *grid = C * std::min(clusters, n);
     return e;
+}
+
+template <int NW>
+cudaError_t resident_launch(int C, int grid, size_t smem, cudaStream_t stream, const ResArgs &P)
+{
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(NW * 32);
+    cfg.gridDim = dim3(grid);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_resident<NW>, P);
 }
 
 }  // namespace
@@ -543,20 +526,16 @@ size_t resident_smem_limit(int blocks)
     return lim;
 }
 
-// Runs the jobs (all fitting cluster size C with nw warps a block) in one launch of k_resident.
-int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+// Host-side preparation of one launch: job table (longest first), stats and
+// control words, and their pristine copies, all in one device allocation.
+int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
+                     bool async_alloc, ResidentPrepared *R)
 {
-    if (n <= 0) return THIN_OK;
-    if (opt.max_phases == 0) {
-        if (out)
-            for (int k = 0; k < n; ++k) {
-                std::memset(&out[k], 0, sizeof out[k]);
-                out[k].status = THIN_ERR_NOT_CONVERGED;
-                out[k].last_change_phase = -1;
-                out[k].end_phase = opt.start_phase;
-            }
-        return THIN_ERR_NOT_CONVERGED;
-    }
+    *R = ResidentPrepared();
+    R->n = n;
+    R->C = C;
+    R->nw = nw;
+    R->async_alloc = async_alloc;
     if (nw != 4 && nw != 8 && nw != 16) return THIN_ERR_ARG;
     const size_t limit = resident_smem_limit(kResMaxWarps / nw);
     std::vector<ResJob> rj(n);
@@ -583,6 +562,7 @@ int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &
         r.wpr = (r.cw + 31) / 32;
         r.bulk = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0) && ((size_t(J.w) * es) % 16 == 0);
         r.index = k;
+        r.adj = J.adj;
         const int held = r.rows + 2 * r.hr;
         const size_t need = res_smem_bytes(held, r.rp, r.wpr, nw);
         if (need > limit || held / 2 * r.cw > 65535) return THIN_ERR_ARG;
@@ -597,73 +577,132 @@ int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &
     });
     std::vector<ResJob> sorted(n);
     for (int k = 0; k < n; ++k) sorted[k] = rj[order[k]];
+    R->order = order;
+    R->smem = smem;
 
     const size_t o_jobs = 0;
+    const size_t st_bytes = (sizeof(ResStat) * n + 255) / 256 * 256;
     const size_t o_st = (sizeof(ResJob) * n + 255) / 256 * 256;
-    const size_t o_ctl = o_st + (sizeof(ResStat) * n + 255) / 256 * 256;
-    const size_t total = o_ctl + 256;
-    char *base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&base), total, stream) != cudaSuccess) {
+    const size_t o_ctl = o_st + st_bytes;
+    const size_t o_st0 = o_ctl + 256;
+    const size_t o_ctl0 = o_st0 + st_bytes;
+    const size_t total = o_ctl0 + 256;
+    cudaError_t e = async_alloc ? cudaMallocAsync(reinterpret_cast<void **>(&R->base), total, stream)
+                                : cudaMalloc(reinterpret_cast<void **>(&R->base), total);
+    if (e != cudaSuccess) {
         cudaGetLastError();
+        R->base = nullptr;
         return THIN_ERR_OOM;
     }
     std::vector<ResStat> st0(n);
-    for (auto &s : st0) {
-        std::memset(&s, 0, sizeof s);
-        s.last_change = -1;
+    for (auto &x : st0) {
+        std::memset(&x, 0, sizeof x);
+        x.last_change = -1;
     }
     ResCtl ctl0;
     std::memset(&ctl0, 0, sizeof ctl0);
-    cudaError_t e = cudaMemcpyAsync(base + o_jobs, sorted.data(), sizeof(ResJob) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_st, st0.data(), sizeof(ResStat) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(R->base + o_jobs, sorted.data(), sizeof(ResJob) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_st0, st0.data(), sizeof(ResStat) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_ctl0, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
+    R->st0 = R->base + o_st0;
+    R->ctl0 = R->base + o_ctl0;
+    R->st_bytes = sizeof(ResStat) * n;
 
-    ResArgs P;
+    ResArgs &P = R->P;
     std::memset(&P, 0, sizeof P);
-    P.jobs = reinterpret_cast<const ResJob *>(base + o_jobs);
-    P.st = reinterpret_cast<ResStat *>(base + o_st);
-    P.ctl = reinterpret_cast<ResCtl *>(base + o_ctl);
+    P.jobs = reinterpret_cast<const ResJob *>(R->base + o_jobs);
+    P.st = reinterpret_cast<ResStat *>(R->base + o_st);
+    P.ctl = reinterpret_cast<ResCtl *>(R->base + o_ctl);
     P.njobs = n;
-    P.rule = opt.rule;
+    P.rule = test_mode(opt);  // F^- reading and operator
     P.start_phase = opt.start_phase;
     P.max_phases = opt.max_phases;
     P.timeout_ns = 2000000000ull;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
-
     if (e == cudaSuccess) {
         switch (nw) {
-        case 4: e = resident_launch<4>(C, n, smem, stream, P); break;
-        case 8: e = resident_launch<8>(C, n, smem, stream, P); break;
-        default: e = resident_launch<16>(C, n, smem, stream, P); break;
+        case 4: e = resident_shape<4>(C, n, smem, &R->grid); break;
+        case 8: e = resident_shape<8>(C, n, smem, &R->grid); break;
+        default: e = resident_shape<16>(C, n, smem, &R->grid); break;
         }
     }
-    int rc = THIN_OK;
-    if (e == cudaSuccess && out) {
-        std::vector<ResStat> st(n);
-        ResCtl ctl;
-        e = cudaMemcpyAsync(st.data(), P.st, sizeof(ResStat) * n, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e == cudaSuccess) {
-            for (int k = 0; k < n; ++k) {
-                const ResStat &S = st[k];
-                thin_stats &o = out[sorted[k].index];
-                std::memset(&o, 0, sizeof o);
-                o.converged = S.converged && !ctl.error;
-                o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
-                o.phases = S.phases;
-                o.lowered = (int64_t)S.lowered;
-                o.last_change_phase = S.last_change;
-                o.end_phase = opt.start_phase + S.phases;
-                o.tiles_visited = 0;
-                o.steps = S.phases;
-                o.tested = (int64_t)S.tested;
-                if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
-            }
-        }
+    return e == cudaSuccess ? THIN_OK : cuda_status(e);
+}
+
+// Resets the stats and control words from their pristine copies and
+// launches: device work only, so it can be captured in a CUDA graph.
+cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemcpyAsync(R.P.st, R.st0, R.st_bytes, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.P.ctl, R.ctl0, sizeof(ResCtl), cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return e;
+    switch (R.nw) {
+    case 4: return resident_launch<4>(R.C, R.grid, R.smem, stream, R.P);
+    case 8: return resident_launch<8>(R.C, R.grid, R.smem, stream, R.P);
+    default: return resident_launch<16>(R.C, R.grid, R.smem, stream, R.P);
     }
-    cudaFreeAsync(base, stream);
+}
+
+// Waits for the stream and writes the stats of job k (the caller's order) to out[k].
+int resident_collect(const ResidentPrepared &R, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    const int n = R.n;
+    std::vector<ResStat> st(n);
+    ResCtl ctl;
+    cudaError_t e = cudaMemcpyAsync(st.data(), R.P.st, sizeof(ResStat) * n, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, R.P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e);
+    int rc = THIN_OK;
+    for (int k = 0; k < n; ++k) {
+        const ResStat &S = st[k];
+        thin_stats &o = out[R.order[k]];
+        std::memset(&o, 0, sizeof o);
+        o.converged = S.converged && !ctl.error;
+        o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
+        o.phases = S.phases;
+        o.lowered = (int64_t)S.lowered;
+        o.last_change_phase = S.last_change;
+        o.end_phase = opt.start_phase + S.phases;
+        o.tiles_visited = 0;
+        o.steps = S.phases;
+        o.tested = (int64_t)S.tested;
+        if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
+    }
+    return rc;
+}
+
+void resident_release(ResidentPrepared &R, cudaStream_t stream)
+{
+    if (R.base) {
+        if (R.async_alloc) cudaFreeAsync(R.base, stream);
+        else cudaFree(R.base);
+    }
+    R.base = nullptr;
+}
+
+// Runs the jobs (all fitting cluster size C with nw warps a block) in one launch of k_resident.
+int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    if (n <= 0) return THIN_OK;
+    if (opt.max_phases == 0) {
+        if (out)
+            for (int k = 0; k < n; ++k) {
+                std::memset(&out[k], 0, sizeof out[k]);
+                out[k].status = THIN_ERR_NOT_CONVERGED;
+                out[k].last_change_phase = -1;
+                out[k].end_phase = opt.start_phase;
+            }
+        return THIN_ERR_NOT_CONVERGED;
+    }
+    ResidentPrepared R;
+    int rc = resident_prepare(jobs, n, C, nw, opt, stream, true, &R);
+    if (rc == THIN_OK) {
+        const cudaError_t e = resident_enqueue(R, stream);
+        if (e != cudaSuccess) rc = cuda_status(e);
+        else if (out) rc = resident_collect(R, opt, stream, out);
+    }
+    resident_release(R, stream);
     return rc;
 }
 

@@ -61,11 +61,17 @@ __device__ __forceinline__ uint32_t merge_dirs(const uint32_t lt[8])
 // T+ = T-- except when no 4-neighbour is lower (T-- = 0) or all eight are
 // (T+ = 0), so "destructible" is "exactly one run start".  k-divergent points
 // (two or more runs) are lambda-destructible when at most one of their
-// counted components fails F(x) - F^-(c) <= lambda.  Returns 0x01 in the
-// bytes of the lambda-destructible points among those set in `vm`.
+// counted components fails F(x) - F^-(c) <= lambda.  mode: bit 0 the F^-
+// reading (0 max, 1 min); bit 1 set asks for the lambda-skeleton's test
+// instead (lambda-deletable and not lambda-end, Sec. 2.1-2.2): a peak point
+// (all eight lower, T+ = 0) also qualifies when F(x) - alpha^- <= lambda, and
+// an end point (exactly one neighbour >= F(x)) is kept when
+// F(x) - alpha^- > lambda.  Returns 0x01 in the bytes of the points that may
+// be lowered, among those set in `vm`.
 __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                            uint32_t lam, int rule, uint32_t &M)
+                                            uint32_t lam, int mode, uint32_t &M)
 {
+    const int rule = mode & 1;
     const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
     uint32_t lt[8];
 #pragma unroll
@@ -100,6 +106,20 @@ __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], ui
         }
         ok |= okdv & dv;
     }
+    if (mode & 2) {
+        // shallow: some lower neighbour >= F(x) - lambda, i.e. F(x) - alpha^- <= lambda
+        const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
+        const uint32_t cl = __vsubus4(c, lrep);
+        const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
+        uint32_t dp[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
+        const uint32_t shallow = nonzero8(M & ~merge_dirs(dp));
+        const uint32_t U = ~M;                                   // neighbours >= F(x), per byte
+        const uint32_t peak = ~nonzero8(U) & kMsb8;              // none: T+ = 0
+        const uint32_t end = nonzero8(U) & ~nonzero8(U & ((U | kMsb8) - kLsb8));  // exactly one
+        ok = (ok | ((peak & shallow) >> 7)) & ~((end & ~shallow) >> 7) & vm;
+    }
     return ok & 0x01010101u;
 }
 
@@ -109,13 +129,13 @@ __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], ui
 // values, `nin` the lowering steps of the points also in `in`.  `comp` is the
 // component-mask table.
 __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
-                                           const uint32_t *comp, uint32_t lam, int rule, int &nin)
+                                           const uint32_t *comp, uint32_t lam, int mode, int &nin)
 {
     uint32_t okacc = 0;
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
         uint32_t M;
-        const uint32_t ok = decide4(c, nb, vm, comp, lam, rule, M);
+        const uint32_t ok = decide4(c, nb, vm, comp, lam, mode, M);
         if (!ok) break;
         // alpha^-: largest lower neighbour, by a tree of byte maxima; direction d
         // of point k is lower iff bit d of byte k of M is set
@@ -178,20 +198,20 @@ __device__ __forceinline__ void gather_u8(const uint8_t *ra, const uint8_t *rb, 
 
 // One u8 work item, tested only: 0x01 in the bytes of the points that would be lowered now.
 __device__ __forceinline__ uint32_t test_u8(const uint8_t *ra, const uint8_t *rb, const uint8_t *rc, int px,
-                                            uint32_t vm, const uint32_t *comp, uint32_t lam, int rule)
+                                            uint32_t vm, const uint32_t *comp, uint32_t lam, int mode)
 {
     uint32_t nb[8], c, other, M;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    return decide4(c, nb, vm, comp, lam, rule, M);
+    return decide4(c, nb, vm, comp, lam, mode, M);
 }
 
 // One u8 work item, lowered: the lowering loop on its four points, the block written back.
 __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
-                                            uint32_t in, const uint32_t *comp, uint32_t lam, int rule, int &nin)
+                                            uint32_t in, const uint32_t *comp, uint32_t lam, int mode, int &nin)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4(c, nb, vm, in, comp, lam, rule, nin);
+    const uint32_t moved = lower4(c, nb, vm, in, comp, lam, mode, nin);
     if (moved) {
         uint2 out;
         if (px == 0)
@@ -203,11 +223,13 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
     return moved;
 }
 
-// One u16 work item: the same four points, one at a time through the point
-// table.  ra, rb, rc point at the block's first pixel in rows y - 1, y, y + 1.
-__device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px,
-                                             uint32_t vm, uint32_t in, const uint32_t *tab, uint32_t lam, int rule,
-                                             int &nin)
+// One work item through the point table (u16 images, and u8 images under
+// (4,8)): the same four points, one at a time.  ra, rb, rc point at the
+// block's first pixel in rows y - 1, y, y + 1; `tab` is the point table of
+// the adjacency pair in mode bit 2.
+template <typename T>
+__device__ __forceinline__ uint32_t item_table(const T *ra, T *rb, const T *rc, int px, uint32_t vm, uint32_t in,
+                                               const uint32_t *tab, uint32_t lam, int mode, int &nin)
 {
     uint32_t moved = 0;
 #pragma unroll 1
@@ -216,14 +238,21 @@ __device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, c
         const int x = px + 2 * k;
         uint32_t nb[8] = {rb[x + 1], ra[x + 1], ra[x], ra[x - 1], rb[x - 1], rc[x - 1], rc[x], rc[x + 1]};
         int nl = 0;
-        const uint32_t c2 = lower_point(rb[x], nb, tab, lam, rule, nl);
+        const uint32_t c2 = lower_point(rb[x], nb, tab, lam, mode, nl);
         if (nl) {
-            rb[x] = static_cast<uint16_t>(c2);
+            rb[x] = static_cast<T>(c2);
             moved |= 1u << (8 * k);
             if ((in >> (8 * k)) & 1u) nin += nl;
         }
     }
     return moved;
+}
+
+__device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px,
+                                             uint32_t vm, uint32_t in, const uint32_t *tab, uint32_t lam, int mode,
+                                             int &nin)
+{
+    return item_table<uint16_t>(ra, rb, rc, px, vm, in, tab, lam, mode, nin);
 }
 
 }  // namespace thin

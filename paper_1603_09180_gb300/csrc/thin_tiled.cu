@@ -60,7 +60,7 @@ struct ImgDesc {
     int w, h, dtype;
     unsigned lam;
     int tiles_x, tiles_y, tile_base, copy_in;
-    int cells_x, cells_y, pad0, pad1;
+    int cells_x, cells_y, adj, pad1;
 };
 
 struct ImgStat {
@@ -110,6 +110,8 @@ struct EngineArgs {
 
 __device__ const PointTable d_point_table = kPointTable;
 __device__ const PointTable d_component_table = kComponentTable;
+__device__ const PointTable d_point_table48 = kPointTable48;
+__device__ const PointTable d_component_table48 = kComponentTable48;
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -305,13 +307,13 @@ __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_
             ntest += __popc(in);
             uint32_t moved;
             T *rb = tile + sr * bw + sb;
-            if (sizeof(T) == 1)
+            if (sizeof(T) == 1 && !(V.rule & 4))  // u8 under (8,4): four points at once
                 moved = item_u8(reinterpret_cast<const uint8_t *>(rb - bw), reinterpret_cast<uint8_t *>(rb),
                                 reinterpret_cast<const uint8_t *>(rb + bw), px, vm, in, tabs + 256, V.lam, V.rule,
                                 nlow);
             else
-                moved = item_u16(reinterpret_cast<const uint16_t *>(rb - bw), reinterpret_cast<uint16_t *>(rb),
-                                 reinterpret_cast<const uint16_t *>(rb + bw), px, vm, in, tabs, V.lam, V.rule, nlow);
+                moved = item_table<T>(rb - bw, rb, rb + bw, px, vm, in, tabs + ((V.rule & 4) ? kTabOffset48 : 0), V.lam,
+                                      V.rule, nlow);
             if (moved) {
                 cells[((sr >> 1) + 1) * ccols + q + 1] = rel;
                 if (moved & in) chg = true;
@@ -358,7 +360,7 @@ __device__ __forceinline__ void decode(const EngineArgs &P, bool full, const uns
     tx = local - ty * D.tiles_x;
 }
 
-constexpr int kSmemTabs = 2048;  // point table (256 x u32) + component table (256 x u32)
+constexpr int kSmemTabs = 4 * kTabWords;  // point and component tables of (8,4) and (4,8), 256 x u32 each
 
 __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
 {
@@ -378,6 +380,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         tabs[i] = d_point_table.v[i];
         tabs[256 + i] = d_component_table.v[i];
+        tabs[kTabOffset48 + i] = d_point_table48.v[i];
+        tabs[kTabOffset48 + 256 + i] = d_component_table48.v[i];
     }
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
             V.w = D.w;
             V.h = D.h;
             V.lam = D.lam;
-            V.rule = P.rule;
+            V.rule = P.rule | (D.adj << 2);  // F^- reading, operator, adjacency pair
             V.tw = P.tw;
             V.th = P.th;
             V.H = H;
@@ -596,19 +600,23 @@ void tiled_defaults(int dtype, int *tw, int *th, int *halo)
     *halo = dtype == THIN_U16 ? 8 : 8;
 }
 
-int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+// A tiled launch prepared on the host: layout, tensor maps and pristine
+// stats/control words uploaded into one device allocation.
+struct TiledPrepared {
+    int n = 0, H = 0, grid = 0, smem = 0;
+    bool async_alloc = true;
+    char *base = nullptr;
+    size_t o_stat = 0, o_ctl = 0, o_stat0 = 0, o_ctl0 = 0, o_listed = 0, o_cells = 0, cells_bytes = 0;
+    int total_tiles = 0;
+    std::vector<JobSpec> jobs;
+    std::vector<ImgDesc> descs;
+    EngineArgs P;
+};
+
+int tiled_prepare(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, bool async_alloc,
+                  TiledPrepared **out)
 {
-    if (n <= 0) return THIN_OK;
-    if (opt.max_phases == 0) {  // nothing may run: every image stays as it is, unconverged
-        if (out)
-            for (int k = 0; k < n; ++k) {
-                std::memset(&out[k], 0, sizeof out[k]);
-                out[k].status = THIN_ERR_NOT_CONVERGED;
-                out[k].last_change_phase = -1;
-                out[k].end_phase = opt.start_phase;
-            }
-        return THIN_ERR_NOT_CONVERGED;
-    }
+    *out = nullptr;
     bool any16 = false;
     for (int k = 0; k < n; ++k) any16 |= jobs[k].dtype == THIN_U16;
     int tw = opt.tile_w, th = opt.tile_h, H = opt.halo;
@@ -632,15 +640,25 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
+    TiledPrepared *T = new TiledPrepared;
+    T->n = n;
+    T->H = H;
+    T->async_alloc = async_alloc;
+    T->jobs.assign(jobs, jobs + n);
     // ---- layout of one scratch allocation
-    std::vector<ImgDesc> descs(n);
+    std::vector<ImgDesc> &descs = T->descs;
+    descs.resize(n);
     std::vector<size_t> buf_off(n), cpy_off(n), cell_off(n);
     size_t off = 0;
     const size_t o_desc = off;
     off = align_up(off + sizeof(ImgDesc) * n, 256);
-    const size_t o_stat = off;
+    T->o_stat = off;
     off = align_up(off + sizeof(ImgStat) * n, 256);
-    const size_t o_ctl = off;
+    T->o_stat0 = off;
+    off = align_up(off + sizeof(ImgStat) * n, 256);
+    T->o_ctl = off;
+    off = align_up(off + sizeof(Ctl), 256);
+    T->o_ctl0 = off;
     off = align_up(off + sizeof(Ctl), 256);
     int total_tiles = 0;
     for (int k = 0; k < n; ++k) {
@@ -651,6 +669,7 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
         D.h = J.h;
         D.dtype = J.dtype;
         D.lam = J.lam;
+        D.adj = J.adj;
         D.tiles_x = (J.w + tw - 1) / tw;
         D.tiles_y = (J.h + th - 1) / th;
         D.tile_base = total_tiles;
@@ -671,32 +690,33 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
             off = align_up(off + D.pitch * J.h, 256);
         }
     }
-    const size_t o_cells = off;
+    T->o_cells = off;
     for (int k = 0; k < n; ++k) {
         cell_off[k] = off;
         off = align_up(off + sizeof(int32_t) * size_t(descs[k].cells_x) * descs[k].cells_y, 256);
     }
-    const size_t cells_bytes = off - o_cells;
-    const size_t o_listed = off;
+    T->cells_bytes = off - T->o_cells;
+    T->o_listed = off;
     off = align_up(off + sizeof(int) * total_tiles, 256);
     const size_t o_lists = off;
     off = align_up(off + sizeof(unsigned) * 3 * size_t(total_tiles), 256);
     const size_t total_bytes = off;
+    T->total_tiles = total_tiles;
 
-    char *base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&base), total_bytes, stream) != cudaSuccess) {
+    cudaError_t e = async_alloc ? cudaMallocAsync(reinterpret_cast<void **>(&T->base), total_bytes, stream)
+                                : cudaMalloc(reinterpret_cast<void **>(&T->base), total_bytes);
+    if (e != cudaSuccess) {
         cudaGetLastError();
+        T->base = nullptr;
+        delete T;
         return THIN_ERR_OOM;
     }
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    char *base = T->base;
+    for (int k = 0; k < n; ++k) {
         ImgDesc &D = descs[k];
         const JobSpec &J = jobs[k];
         void *b0 = D.copy_in ? static_cast<void *>(base + cpy_off[k]) : J.img;
         void *b1 = base + buf_off[k];
-        if (D.copy_in)
-            e = cudaMemcpy2DAsync(b0, D.pitch, J.img, J.pitch, size_t(J.w) * elem_size(J.dtype), J.h,
-                                  cudaMemcpyDeviceToDevice, stream);
         D.buf[0] = reinterpret_cast<unsigned long long>(b0);
         D.buf[1] = reinterpret_cast<unsigned long long>(b1);
         D.cells = reinterpret_cast<unsigned long long>(base + cell_off[k]);
@@ -711,95 +731,163 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
                              2, bp, gdim, gstr, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) {
-                cudaFreeAsync(base, stream);
+                tiled_release(T, stream);
                 return THIN_ERR_ARG;
             }
         }
     }
     std::vector<ImgStat> st0(n);
-    for (auto &s : st0) {
-        s.lowered = 0;
-        s.tiles_visited = 0;
-        s.tested = 0;
-        s.last_change = -1;
-        s.last_step = -1;
-        s.last_listed = 0;
+    for (auto &x : st0) {
+        x.lowered = 0;
+        x.tiles_visited = 0;
+        x.tested = 0;
+        x.last_change = -1;
+        x.last_step = -1;
+        x.last_listed = 0;
     }
     Ctl ctl0;
     std::memset(&ctl0, 0, sizeof ctl0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_desc, descs.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_stat, st0.data(), sizeof(ImgStat) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_listed, 0xff, sizeof(int) * total_tiles, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_cells, 0, cells_bytes, stream);  // every cell: changed at the first phase
+    e = cudaMemcpyAsync(base + o_desc, descs.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + T->o_stat0, st0.data(), sizeof(ImgStat) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + T->o_ctl0, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
 
-    EngineArgs P;
+    EngineArgs &P = T->P;
     std::memset(&P, 0, sizeof P);
     P.imgs = reinterpret_cast<const ImgDesc *>(base + o_desc);
-    P.st = reinterpret_cast<ImgStat *>(base + o_stat);
-    P.listed = reinterpret_cast<int *>(base + o_listed);
+    P.st = reinterpret_cast<ImgStat *>(base + T->o_stat);
+    P.listed = reinterpret_cast<int *>(base + T->o_listed);
     P.lists = reinterpret_cast<unsigned *>(base + o_lists);
-    P.ctl = reinterpret_cast<Ctl *>(base + o_ctl);
+    P.ctl = reinterpret_cast<Ctl *>(base + T->o_ctl);
     P.n_imgs = n;
     P.total_tiles = total_tiles;
     P.tw = tw;
     P.th = th;
     P.halo = H;
     P.hr = HR;
-    P.rule = opt.rule;
+    P.rule = test_mode(opt);  // F^- reading and operator
     P.start_phase = opt.start_phase;
     P.max_phases = opt.max_phases;
     P.timeout_ns = 2000000000ull;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
     P.debug = opt.reserved;
     P.wl = warp_layout(tw, th, HR, any16);
-    const int smem = 128 + kSmemTabs + kWarps * P.wl.bytes;
+    T->smem = 128 + kSmemTabs + kWarps * P.wl.bytes;
+    {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(k_engine)) == cudaSuccess &&
+            size_t(T->smem) + fa.sharedSizeBytes > size_t(optin)) {
+            tiled_release(T, stream);
+            return THIN_ERR_ARG;  // this tile shape and halo do not fit one block's shared memory
+        }
+    }
 
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_engine));
     int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, T->smem);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    int grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
-    if (opt.reserved == 1) grid = std::max(grid, std::min(2, sms * per_sm));
+    T->grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
+    if (opt.reserved == 1) T->grid = std::max(T->grid, std::min(2, sms * per_sm));
+    if (e != cudaSuccess) {
+        tiled_release(T, stream);
+        return cuda_status(e);
+    }
+    *out = T;
+    return THIN_OK;
+}
+
+// Copies unaligned images in, resets the per-run state, launches the engine
+// and the copy-out: device work only, so it can be captured in a CUDA graph.
+cudaError_t tiled_enqueue(const TiledPrepared *T, cudaStream_t stream)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < T->n && e == cudaSuccess; ++k) {
+        const ImgDesc &D = T->descs[k];
+        const JobSpec &J = T->jobs[k];
+        if (D.copy_in)
+            e = cudaMemcpy2DAsync(reinterpret_cast<void *>(D.buf[0]), D.pitch, J.img, J.pitch,
+                                  size_t(J.w) * elem_size(J.dtype), J.h, cudaMemcpyDeviceToDevice, stream);
+    }
+    char *base = T->base;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + T->o_stat, base + T->o_stat0, sizeof(ImgStat) * T->n, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + T->o_ctl, base + T->o_ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + T->o_listed, 0xff, sizeof(int) * T->total_tiles, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + T->o_cells, 0, T->cells_bytes, stream);  // every cell: changed at the first phase
     if (e == cudaSuccess) {
-        void *args[] = {&P};
-        e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_engine), dim3(grid), dim3(kThreads), args, smem,
+        void *args[] = {const_cast<EngineArgs *>(&T->P)};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_engine), dim3(T->grid), dim3(kThreads), args, T->smem,
                                         stream);
     }
     if (e == cudaSuccess) {
-        k_copy_out<<<dim3(64, n), 256, 0, stream>>>(P.imgs, P.st, n);
+        k_copy_out<<<dim3(64, T->n), 256, 0, stream>>>(T->P.imgs, T->P.st, T->n);
         e = cudaGetLastError();
     }
-    int rc = THIN_OK;
-    if (e == cudaSuccess && out) {
-        std::vector<ImgStat> st(n);
-        Ctl ctl;
-        e = cudaMemcpyAsync(st.data(), P.st, sizeof(ImgStat) * n, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e == cudaSuccess) {
-            for (int k = 0; k < n; ++k) {
-                const ImgStat &S = st[k];
-                thin_stats &o = out[k];
-                std::memset(&o, 0, sizeof o);
-                const long long steps = S.last_step + 1;
-                long long phases = steps * H;
-                if (opt.max_phases >= 0) phases = std::min<long long>(phases, opt.max_phases);
-                o.converged = (S.last_listed <= S.last_step && ctl.error == 0) ? 1 : 0;
-                o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
-                o.phases = phases;
-                o.lowered = (int64_t)S.lowered;
-                o.last_change_phase = S.last_change;
-                o.end_phase = opt.start_phase + phases;
-                o.tiles_visited = (int64_t)S.tiles_visited;
-                o.tested = (int64_t)S.tested;
-                o.steps = steps;
-                if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
-            }
-        }
-    }
-    cudaFreeAsync(base, stream);
+    return e;
+}
+
+int tiled_collect(const TiledPrepared *T, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    const int n = T->n;
+    std::vector<ImgStat> st(n);
+    Ctl ctl;
+    cudaError_t e = cudaMemcpyAsync(st.data(), T->P.st, sizeof(ImgStat) * n, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, T->P.ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e);
+    int rc = THIN_OK;
+    for (int k = 0; k < n; ++k) {
+        const ImgStat &S = st[k];
+        thin_stats &o = out[k];
+        std::memset(&o, 0, sizeof o);
+        const long long steps = S.last_step + 1;
+        long long phases = steps * T->H;
+        if (opt.max_phases >= 0) phases = std::min<long long>(phases, opt.max_phases);
+        o.converged = (S.last_listed <= S.last_step && ctl.error == 0) ? 1 : 0;
+        o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
+        o.phases = phases;
+        o.lowered = (int64_t)S.lowered;
+        o.last_change_phase = S.last_change;
+        o.end_phase = opt.start_phase + phases;
+        o.tiles_visited = (int64_t)S.tiles_visited;
+        o.tested = (int64_t)S.tested;
+        o.steps = steps;
+        if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
+    }
+    return rc;
+}
+
+void tiled_release(TiledPrepared *T, cudaStream_t stream)
+{
+    if (!T) return;
+    if (T->base) {
+        if (T->async_alloc) cudaFreeAsync(T->base, stream);
+        else cudaFree(T->base);
+    }
+    delete T;
+}
+
+int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, thin_stats *out)
+{
+    if (n <= 0) return THIN_OK;
+    if (opt.max_phases == 0) {  // nothing may run: every image stays as it is, unconverged
+        if (out)
+            for (int k = 0; k < n; ++k) {
+                std::memset(&out[k], 0, sizeof out[k]);
+                out[k].status = THIN_ERR_NOT_CONVERGED;
+                out[k].last_change_phase = -1;
+                out[k].end_phase = opt.start_phase;
+            }
+        return THIN_ERR_NOT_CONVERGED;
+    }
+    TiledPrepared *T = nullptr;
+    int rc = tiled_prepare(jobs, n, opt, stream, true, &T);
+    if (rc != THIN_OK) return rc;
+    const cudaError_t e = tiled_enqueue(T, stream);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    else if (out) rc = tiled_collect(T, opt, stream, out);
+    tiled_release(T, stream);
     return rc;
 }
 
@@ -881,6 +969,7 @@ int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t st
     D.h = J.h;
     D.dtype = J.dtype;
     D.lam = J.lam;
+    D.adj = J.adj;
     D.tiles_x = (J.w + tw - 1) / tw;
     D.tiles_y = (J.h + th - 1) / th;
     D.tile_base = 0;
@@ -969,7 +1058,7 @@ int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t st
     P.th = th;
     P.halo = H;
     P.hr = HR;
-    P.rule = opt.rule;
+    P.rule = test_mode(opt);  // F^- reading and operator
     P.start_phase = opt.start_phase;
     P.max_phases = opt.max_phases;
     P.timeout_ns = 2000000000ull;
@@ -978,10 +1067,14 @@ int tiled_run_noalloc(const JobSpec &J, const thin_options &opt, cudaStream_t st
     P.wl = warp_layout(tw, th, HR, is16);
     const int smem = 128 + kSmemTabs + kWarps * P.wl.bytes;
 
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, optin = 0;
+    cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(k_engine));
+    if (e == cudaSuccess && size_t(smem) + fa.sharedSizeBytes > size_t(optin)) return THIN_ERR_ARG;
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_engine));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, smem);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     const int grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
@@ -1031,9 +1124,9 @@ extern "C" int thin_run_noalloc(void *img_dev, int w, int h, size_t pitch_bytes,
     thin_options o;
     thin_default_options(&o);
     if (opt) o = *opt;
-    if (adj == THIN_ADJ_4_8) return THIN_ERR_UNSUPPORTED;
-    if (adj != THIN_ADJ_8_4) return THIN_ERR_ARG;
+    if (adj != THIN_ADJ_8_4 && adj != THIN_ADJ_4_8) return THIN_ERR_ARG;
     if (o.rule != THIN_RULE_MAX && o.rule != THIN_RULE_MIN) return THIN_ERR_ARG;
+    if (o.op != THIN_OP_THINNING && o.op != THIN_OP_SKELETON) return THIN_ERR_ARG;
     if (o.start_phase < 0 || o.tile_w < 0 || o.tile_h < 0 || o.halo < 0) return THIN_ERR_ARG;
     if (w < 0 || h < 0 || (dt != THIN_U8 && dt != THIN_U16)) return THIN_ERR_ARG;
     const size_t es = dt == THIN_U16 ? 2 : 1;
@@ -1050,6 +1143,6 @@ extern "C" int thin_run_noalloc(void *img_dev, int w, int h, size_t pitch_bytes,
         }
         return THIN_OK;
     }
-    thin::JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda};
+    thin::JobSpec j{img_dev, w, h, pitch_bytes, int(dt), lambda, int(adj)};
     return thin::tiled_run_noalloc(j, o, static_cast<cudaStream_t>(stream), out);
 }

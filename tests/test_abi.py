@@ -36,11 +36,14 @@ def test_exports_every_declared_symbol(lib):
     assert "sm_103a" in thin.version()
 
 
-def test_point_table_matches_oracle():
-    tab = thin.point_table()
+@pytest.mark.parametrize("adj", [thin.ADJ_8_4, thin.ADJ_4_8])
+def test_point_table_matches_oracle(adj):
+    tab = thin.point_table(adj)
+    if adj == thin.ADJ_8_4:
+        assert tab == thin.point_table()
     for m in range(256):
         e = tab[m]
-        tp, tm, lab = oracle.mask_numbers(m)
+        tp, tm, lab = oracle.mask_numbers(m, adj=adj)
         assert (e & 7, (e >> 3) & 7) == (tp, tm), m
         assert bool(e >> 30 & 1) == (tp == 1 and tm == 1)
         assert bool(e >> 31 & 1) == (tm >= 2)
@@ -61,7 +64,7 @@ def test_host_side_argument_errors(lib):
     assert run(ctypes.c_void_p(4096), 10, 10, 9, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
     assert run(ctypes.c_void_p(4096), 10, 10, 20, 7, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
     assert run(ctypes.c_void_p(4097), 10, 10, 20, thin.U16, 0, thin.ADJ_8_4, None) == thin.THIN_ERR_ARG
-    assert run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, thin.ADJ_4_8, None) == thin.THIN_ERR_UNSUPPORTED
+    assert run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, 7, None) == thin.THIN_ERR_ARG  # no such adjacency pair
     assert run(ctypes.c_void_p(4096), 10, 10, 10, thin.U8, 0, 9, None) == thin.THIN_ERR_ARG
     # empty and interior-free images are valid no-ops that touch no memory
     assert run(None, 0, 0, 0, thin.U8, 0, thin.ADJ_8_4, None) == thin.THIN_OK
@@ -98,3 +101,32 @@ def test_missing_library_fails_loudly(tmp_path):
             mod.load(str(tmp_path / "nope.so"))
         finally:
             mod._lib = saved
+
+
+def test_serve_host_side_errors(lib):
+    h = ctypes.c_void_p()
+    assert lib.thin_serve_create(0, 4, 4, ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_create(1 << 20, 0, 4, ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_create(1 << 20, 4, 0, ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_create(1 << 20, 4, 4, None) == thin.THIN_ERR_ARG
+    t = ctypes.c_uint64()
+    done = ctypes.c_int()
+    assert lib.thin_serve_submit(None, None, 4, 4, 4, thin.U8, 0, ctypes.byref(t)) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_poll(None, 1, None, 0, ctypes.byref(done), None) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_wait_any(None, 0, ctypes.byref(t)) == thin.THIN_ERR_ARG
+    assert lib.thin_serve_destroy(None) == thin.THIN_ERR_ARG
+
+
+def test_plan_host_side_errors(lib):
+    h = ctypes.c_void_p()
+    o = thin.options()
+    assert lib.thin_plan_create(None, -1, thin.ADJ_8_4, ctypes.byref(o), ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_plan_create(None, 0, 5, ctypes.byref(o), ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_plan_create(None, 0, thin.ADJ_8_4, ctypes.byref(o), None) == thin.THIN_ERR_ARG
+    naive = thin.options(kernel="naive")
+    assert lib.thin_plan_create(None, 0, thin.ADJ_8_4, ctypes.byref(naive), ctypes.byref(h)) == thin.THIN_ERR_UNSUPPORTED
+    jobs = (thin.Job * 1)()
+    jobs[0].img_dev, jobs[0].w, jobs[0].h, jobs[0].pitch, jobs[0].dtype = 4096, 8, 8, 8, 7
+    assert lib.thin_plan_create(jobs, 1, thin.ADJ_8_4, ctypes.byref(o), ctypes.byref(h)) == thin.THIN_ERR_ARG
+    assert lib.thin_plan_launch(None, None) == thin.THIN_ERR_ARG
+    assert lib.thin_plan_destroy(None) == thin.THIN_ERR_ARG

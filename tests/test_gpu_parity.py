@@ -29,7 +29,9 @@ def check(img, lam, rule="max", **kw):
     st = thin.run(t, lam, rule=rule, **kw)
     torch.cuda.synchronize()
     ref, rst = oracle.thin(img, lam, oracle.RULE_MAX if rule == "max" else oracle.RULE_MIN,
-                           start_phase=kw.get("start_phase", 0), max_phases=kw.get("max_phases", -1))
+                           start_phase=kw.get("start_phase", 0), max_phases=kw.get("max_phases", -1),
+                           op=oracle.OP_SKELETON if kw.get("op") == "skeleton" else oracle.OP_THIN,
+                           adj=kw.get("adj", thin.ADJ_8_4))
     got = to_host(t)
     assert np.array_equal(got, ref), "mismatch at %s" % (np.argwhere(got != ref)[:5].tolist(),)
     assert st["lowered"] == rst["lowered"]
@@ -214,3 +216,94 @@ def test_tested_counts():
     for kernel in ("tiled", "resident"):
         st, _ = check(img, 6, kernel=kernel)
         assert 0 < st["tested"] <= st_n["tested"] + 4 * 128 * 168  # the last quiet phases may run past
+
+
+# ---------------------------------------------------------------- lambda-skeleton (Sec. 2.2)
+
+@pytest.mark.parametrize("kernel", ["naive", "tiled", "resident"])
+@pytest.mark.parametrize("shape", [(3, 40), (17, 33), (65, 129), (128, 200)])
+@pytest.mark.parametrize("lam", [0, 5, 20])
+def test_skeleton_matches_oracle(shape, lam, kernel):
+    img = synth.value_noise_image(*shape, "u8", seed=shape[0] * 5 + shape[1] + lam)
+    check(img, lam, kernel=kernel, op="skeleton")
+
+
+@pytest.mark.parametrize("kernel", ["naive", "tiled", "resident"])
+@pytest.mark.parametrize("dt,vmax,lam,rule", [("u16", 4095, 0, "max"), ("u16", 4095, 30, "min"), ("u8", 255, 255, "max"),
+                                              ("u8", 255, 12, "min")])
+def test_skeleton_value_ranges_and_rules(dt, vmax, lam, rule, kernel):
+    img = synth.value_noise_image(96, 120, dt, seed=vmax + lam + 3, vmax=vmax)
+    check(img, lam, rule=rule, kernel=kernel, op="skeleton")
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_skeleton_lines_and_peaks(kernel):
+    """Thin bright lines and isolated peaks of known contrast (white noise below
+    them): lines with contrast above lambda keep their end points."""
+    rng = np.random.default_rng(6)
+    img = rng.integers(0, 30, (120, 160)).astype(np.uint8)
+    for k in range(10):
+        y, x = int(rng.integers(5, 110)), int(rng.integers(5, 120))
+        img[y, x:x + 30] = 60 + 15 * k
+        img[int(rng.integers(2, 118)), int(rng.integers(2, 158))] = 40 + 20 * k
+    for lam in (0, 50, 120):
+        check(img, lam, kernel=kernel, op="skeleton")
+        check(img, lam, kernel=kernel, op="skeleton", max_phases=6)
+
+
+def test_skeleton_batch_and_plan_match_oracle():
+    imgs = [synth.value_noise_image(h, w, dt, seed=h + w) for h, w, dt in
+            [(40, 50, "u8"), (300, 200, "u8"), (90, 70, "u16"), (700, 650, "u8"), (1000, 2100, "u8")]]
+    lams = [0, 10, 64, 5, 3]
+    refs = [oracle.thin(a, l, op=oracle.OP_SKELETON) for a, l in zip(imgs, lams)]
+    ts = [to_dev(a) for a in imgs]
+    sts, rc = thin.batch(ts, lams, op="skeleton")
+    assert rc == 0
+    for t, (ref, rst), st in zip(ts, refs, sts):
+        assert np.array_equal(to_host(t), ref) and st["lowered"] == rst["lowered"]
+    ts = [to_dev(a) for a in imgs]
+    plan = thin.GraphPlan(ts, lams, op="skeleton")
+    sts, rc = plan.run(stats=True)
+    assert rc == 0
+    for t, (ref, rst), st in zip(ts, refs, sts):
+        assert np.array_equal(to_host(t), ref) and st["lowered"] == rst["lowered"]
+    plan.close()
+
+
+# ---------------------------------------------------------------- (4,8)-adjacency (Sec. 2.1)
+
+@pytest.mark.parametrize("kernel", ["naive", "tiled", "resident"])
+@pytest.mark.parametrize("dt", ["u8", "u16"])
+@pytest.mark.parametrize("op", ["thinning", "skeleton"])
+@pytest.mark.parametrize("lam", [0, 9])
+def test_48_matches_oracle(kernel, dt, op, lam):
+    img = synth.value_noise_image(70, 133, dt, seed=48 + lam)
+    check(img, lam * (16 if dt == "u16" else 1), kernel=kernel, op=op, adj=thin.ADJ_4_8)
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+def test_48_sizes_noise_and_cap(kernel):
+    for shape in [(3, 3), (5, 40), (64, 64), (129, 65)]:
+        check(synth.value_noise_image(*shape, "u8", seed=sum(shape)), 4, kernel=kernel, adj=thin.ADJ_4_8)
+    noise = synth.uniform_noise_image(90, 110, "u8", seed=3)
+    check(noise, 0, kernel=kernel, adj=thin.ADJ_4_8)
+    check(noise, 30, kernel=kernel, adj=thin.ADJ_4_8, max_phases=7)
+
+
+def test_48_batch_plan_and_full_size():
+    imgs = [synth.value_noise_image(h, w, dt, seed=h * w) for h, w, dt in
+            [(50, 60, "u8"), (512, 512, "u8"), (300, 260, "u16"), (1000, 2100, "u8")]]
+    lams = [3, 0, 40, 5]
+    refs = [oracle.thin(a, l, adj=oracle.ADJ_4_8) for a, l in zip(imgs, lams)]
+    for mk in ("batch", "plan"):
+        ts = [to_dev(a) for a in imgs]
+        if mk == "batch":
+            sts, rc = thin.batch(ts, lams, adj=thin.ADJ_4_8)
+        else:
+            plan = thin.GraphPlan(ts, lams, adj=thin.ADJ_4_8)
+            sts, rc = plan.run(stats=True)
+            plan.close()
+        assert rc == 0
+        for t, (ref, rst), st in zip(ts, refs, sts):
+            assert np.array_equal(to_host(t), ref), mk
+            assert st["lowered"] == rst["lowered"]
