@@ -416,39 +416,49 @@ def run_large(args):
             es = work.element_size()
             for lam in lams:
                 work.copy_(pristine)
-                st = thin.run(work, lam, kernel="tiled")
+                st = thin.run(work, lam)  # the default engine: wide resident if the image fits, else tiled
+                engine = "tiled" if st["tiles_visited"] else "resident (wide)"
                 tw, th, H = 64, 32, 8
-                ms = _timed(lambda: thin.run(work, lam, kernel="tiled", stats=False), lambda: work.copy_(pristine),
+                ms = _timed(lambda: thin.run(work, lam, stats=False), lambda: work.copy_(pristine),
                             flush, stream, args.steps, args.warmup)
                 t = statistics.median(ms) / 1e3
-                active = st["tiles_visited"] * tw * th * H / 4.0  # pixel-rounds over active tiles
+                # pixel-rounds over active tiles (tiled) or tested pixel-rounds (resident: a point is tested
+                # at most once per round, and only while a neighbour moved)
+                active = st["tiles_visited"] * tw * th * H / 4.0 if st["tiles_visited"] else float(st["tested"])
                 full = w * h * st["phases"] / 4.0
-                results.append({
-                    "image": "%dx%d %s" % (w, h, dt), "lambda": lam, "ms": round(t * 1e3, 3), "phases": st["phases"],
-                    "tiles_visited": st["tiles_visited"], "tested": st["tested"],
-                    "gpix_sweeps_per_s": round(active / t / 1e9, 2),
-                    "gpix_sweeps_full_per_s": round(full / t / 1e9, 2),
-                    "point_tests_per_s_g": round(st["tested"] / t / 1e9, 2),
-                    "achieved_gbs": round(2 * es * active / t / 1e9, 1),
-                    "frac": round(2 * es * active / t / 1e9 / peak, 4)})
-            if dt == "u8":  # halo sweep on 4096^2 u8, lambda 30
+                r = {"image": "%dx%d %s" % (w, h, dt), "lambda": lam, "engine": engine, "ms": round(t * 1e3, 3),
+                     "phases": st["phases"], "tiles_visited": st["tiles_visited"], "tested": st["tested"],
+                     "gpix_sweeps_per_s": round(active / t / 1e9, 2),
+                     "gpix_sweeps_full_per_s": round(full / t / 1e9, 2),
+                     "point_tests_per_s_g": round(st["tested"] / t / 1e9, 2),
+                     "achieved_gbs": round(2 * es * active / t / 1e9, 1),
+                     "frac": round(2 * es * active / t / 1e9 / peak, 4)}
+                if engine != "tiled":  # the tiled engine on the same image, for comparison
+                    ms_t = _timed(lambda: thin.run(work, lam, kernel="tiled", stats=False),
+                                  lambda: work.copy_(pristine), flush, stream, max(1, args.steps // 2), 1)
+                    r["tiled_ms"] = round(statistics.median(ms_t), 3)
+                results.append(r)
+            if dt == "u8":  # the tiled engine's halo depth, 4096^2 u8, lambda 30
                 sweep = {}
-                for H in (3, 4, 5, 6, 7, 8):
-                    ms = _timed(lambda: thin.run(work, 30, kernel="tiled", halo=H, stats=False),
+                for H in (3, 4, 6, 8, 12, 16):
+                    ms = _timed(lambda: thin.run(work, 30, kernel="tiled", tile=(64, 32) if H <= 8 else (64, 48),
+                                                 halo=H, stats=False),
                                 lambda: work.copy_(pristine), flush, stream, 1, 1)
                     sweep[H] = round(ms[0], 3)
-                results[-1]["halo_sweep_ms"] = sweep
+                results[-1]["tiled_halo_sweep_ms"] = sweep
             del pristine, work
             torch.cuda.empty_cache()
     head = results[1]
-    return {"metric": "Gpix-sweeps/s (4096^2 u8, lambda 30, active tiles)", "value": head["gpix_sweeps_per_s"],
+    return {"metric": "Gpix-sweeps/s (4096^2 u8, lambda 30)", "value": head["gpix_sweeps_per_s"],
             "unit": "Gpix-sweeps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "u8/u16", "data": "synthetic", "workload": "large",
-            "config": {"workload": "4096x4096 u8 and 8192x8192 u16 (0..4095), lambda 0 and 30, tiled engine "
-                                   "64x32 tiles, halo 8", "l2": "flushed before every timed run"},
+            "config": {"workload": "4096x4096 u8 and 8192x8192 u16 (0..4095), lambda 0 and 30, default engine "
+                                   "(wide resident where the image fits the GPU's shared memory, else tiled 64x32, "
+                                   "halo 8)", "l2": "flushed before every timed run"},
             "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": head["frac"], "peak_source": src,
-                         "note": "2 B (u8) or 4 B (u16) per pixel-round over active tiles"},
+                         "note": "2 B (u8) or 4 B (u16) per pixel-round over active tiles (tiled) or per tested "
+                                 "pixel-round (resident)"},
             "cases": results, "clocks": clk.summary()}
 
 

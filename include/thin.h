@@ -74,11 +74,14 @@ typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
  *                   (an end point of F_k, k = F(x), with F(x) - alpha^- > lambda). */
 typedef enum { THIN_OP_THINNING = 0, THIN_OP_SKELETON = 1 } thin_op;
 
-/* Kernel family.  RESIDENT holds each image in the shared memory of one
- * thread-block cluster (images up to about 1.7 MB); TILED streams 64 x 32
- * tiles through shared memory (any size); AUTO picks RESIDENT for images that
- * fit and TILED for the rest; NAIVE runs one launch per phase straight from
- * global memory (the reference slice). */
+/* Kernel family.  RESIDENT holds each image in shared memory for its whole
+ * run: in one thread-block cluster (images up to about 1.7 MB), or, in the
+ * wide mode, in several clusters of one cooperative launch (one block per SM,
+ * clusters of 8, 4, 2 or 1 blocks, whichever lets every strip be resident)
+ * that exchange boundary rows every 8 phases: images up to about 30 MB.  TILED streams 64 x 32 tiles through shared memory (any
+ * size).  AUTO picks RESIDENT for images that fit a cluster, the wide mode
+ * for up to two larger images in a call, and TILED for the rest.  NAIVE runs
+ * one launch per phase straight from global memory (the reference slice). */
 typedef enum {
     THIN_KERNEL_AUTO = 0,
     THIN_KERNEL_NAIVE = 1,

@@ -62,10 +62,13 @@ int check_image(const void *img, int w, int h, size_t pitch, int dt)
 // (AUTO, RESIDENT); the rest go to the tiled engine (AUTO, TILED).  When few
 // images fit, each is spread over a wider cluster (at least 32 rows a block)
 // so that more SMs work on it.
-int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G)
+constexpr int kWideMax = 2;
+
+int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G, bool allow_wide)
 {
     const int n = int(specs.size());
     G->resident.clear();
+    G->wide.clear();
     G->tiled.clear();
     G->nw = 16;  // warps per resident block (one block per SM measured fastest)
     std::vector<int> cls(n, 0);
@@ -90,8 +93,24 @@ int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Groupin
         }
         if (!idx.empty()) G->resident.push_back({C, idx});
     }
-    for (int k = 0; k < n; ++k)
-        if (cls[k] == 0) G->tiled.push_back(k);
+    // Images too large for a cluster: the wide resident mode (the image held
+    // by several clusters of one launch) when at most kWideMax of them are in
+    // the call, each then having most of the GPU; the tiled engine otherwise.
+    std::vector<int> strips(n, 0), csize(n, 0);
+    if (allow_wide && (o.kernel == THIN_KERNEL_AUTO || o.kernel == THIN_KERNEL_RESIDENT)) {
+        const size_t limit = resident_smem_limit(16 / G->nw);
+        for (int k = 0; k < n; ++k)
+            if (cls[k] == 0)
+                strips[k] = resident_wide_strips(specs[k].w, specs[k].h, specs[k].dtype, limit, G->nw, &csize[k]);
+    }
+    int nwide = 0;
+    for (int k = 0; k < n; ++k) nwide += cls[k] == 0 && strips[k] > 0;
+    const bool use_wide = nwide > 0 && (nwide <= kWideMax || o.kernel == THIN_KERNEL_RESIDENT);
+    for (int k = 0; k < n; ++k) {
+        if (cls[k] != 0) continue;
+        if (use_wide && strips[k] > 0) G->wide.push_back({k, strips[k], csize[k]});
+        else G->tiled.push_back(k);
+    }
     if (!G->tiled.empty() && o.kernel == THIN_KERNEL_RESIDENT) return THIN_ERR_ARG;  // does not fit on chip
     return THIN_OK;
 }
@@ -142,6 +161,12 @@ int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, 
         const int rc = resident_prepare(js.data(), int(js.size()), grp.first, G.nw, o, s, async_alloc, &res.back());
         if (rc != THIN_OK) return rc;
     }
+    for (const auto &wj : G.wide) {
+        wide.emplace_back();
+        wide_idx.push_back(wj.job);
+        const int rc = resident_prepare(&specs[wj.job], 1, wj.C, G.nw, o, s, async_alloc, &wide.back(), wj.strips);
+        if (rc != THIN_OK) return rc;
+    }
     if (!G.tiled.empty()) {
         std::vector<JobSpec> js;
         for (int k : G.tiled) js.push_back(specs[k]);
@@ -153,9 +178,9 @@ int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, 
 }
 
 // Resident groups run side by side on helper streams forked from s (a
-// group's clusters take SMs as another group's finish); the tiled group,
-// whose grid barrier needs all its blocks resident at once, runs after them
-// on s.
+// group's clusters take SMs as another group's finish); the wide launches and
+// the tiled group, whose grid barriers need all their blocks resident at
+// once, run after them on s, one after another.
 cudaError_t Execution::enqueue(cudaStream_t s, cudaStream_t *side, cudaEvent_t *ev) const
 {
     cudaError_t e = cudaSuccess;
@@ -171,6 +196,7 @@ cudaError_t Execution::enqueue(cudaStream_t s, cudaStream_t *side, cudaEvent_t *
         }
         for (int g = 0; g < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(s, ev[1 + g], 0);
     }
+    for (size_t w = 0; w < wide.size() && e == cudaSuccess; ++w) e = resident_enqueue(wide[w], s);
     if (e == cudaSuccess && tiled) e = tiled_enqueue(tiled, s);
     return e;
 }
@@ -182,6 +208,12 @@ int Execution::collect(cudaStream_t s, thin_stats *out) const
         std::vector<thin_stats> st(res_idx[g].size());
         const int r = resident_collect(res[g], opt, s, st.data());
         for (size_t k = 0; k < st.size(); ++k) out[res_idx[g][k]] = st[k];
+        if (r != THIN_OK && (rc == THIN_OK || rc == THIN_ERR_NOT_CONVERGED)) rc = r;
+    }
+    for (size_t w = 0; w < wide.size(); ++w) {
+        thin_stats st;
+        const int r = resident_collect(wide[w], opt, s, &st);
+        out[wide_idx[w]] = st;
         if (r != THIN_OK && (rc == THIN_OK || rc == THIN_ERR_NOT_CONVERGED)) rc = r;
     }
     if (tiled) {
@@ -197,6 +229,8 @@ void Execution::release(cudaStream_t s)
 {
     for (auto &r : res) resident_release(r, s);
     res.clear();
+    for (auto &r : wide) resident_release(r, s);
+    wide.clear();
     if (tiled) tiled_release(tiled, s);
     tiled = nullptr;
 }
@@ -205,7 +239,8 @@ namespace {
 
 // Runs validated images in one device-driven pass: every launch group
 // prepared, enqueued side by side, stats collected if asked for.
-int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out)
+int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out,
+             bool allow_wide = true)
 {
     if (o.max_phases == 0) {  // nothing may run: every image stays as it is, unconverged
         if (out)
@@ -218,7 +253,7 @@ int dispatch(const std::vector<JobSpec> &specs, const thin_options &o, cudaStrea
         return THIN_ERR_NOT_CONVERGED;
     }
     Grouping G;
-    int rc = group_jobs(specs, o, &G);
+    int rc = group_jobs(specs, o, &G, allow_wide);
     if (rc != THIN_OK) return rc;
     SideStreams *ss = nullptr;
     if (G.resident.size() > 1) {
@@ -245,6 +280,13 @@ void noop_stats(const thin_options &o, thin_stats *s)
 }
 
 }  // namespace
+
+int batch_validated(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out,
+                    bool allow_wide)
+{
+    return dispatch(specs, o, s, out, allow_wide);
+}
+
 }  // namespace thin
 
 using namespace thin;

@@ -69,7 +69,9 @@ struct ResStat {
 struct ResCtl {
     unsigned next_job;
     int error;
-    int pad[2];
+    unsigned bar_count;  // grid barrier of a wide launch
+    unsigned bar_gen;
+    long long gl_last;   // wide launch: last phase that lowered a point anywhere, -1 if none
 };
 
 struct ResArgs {
@@ -81,13 +83,19 @@ struct ResArgs {
     long long start_phase;
     long long max_phases;
     unsigned long long timeout_ns;
+    // Wide launch (strips > 0): one image over `strips` clusters, cluster s
+    // holding strip s; boundary rows cross between clusters through xbuf.
+    int strips;
+    int pad;
+    unsigned char *xbuf;        // per block: 2 sides x 2 step parities x xslot bytes
+    unsigned long long xslot;
 };
 
 // A resident launch prepared on the host (device tables uploaded), ready to
 // be enqueued any number of times: see resident_prepare / _enqueue /
 // _collect / _release.
 struct ResidentPrepared {
-    int n = 0, C = 0, nw = 0, grid = 0;
+    int n = 0, C = 0, nw = 0, grid = 0, strips = 0;
     size_t smem = 0;
     bool async_alloc = true;
     char *base = nullptr;         // one device allocation holding everything below
@@ -96,8 +104,10 @@ struct ResidentPrepared {
     std::vector<int> order;       // launch position -> index in the prepared job list
     ResArgs P;                    // the kernel's argument block
 };
+// strips > 0: one image (n == 1) over `strips` clusters of C blocks, one
+// cooperative launch (the wide mode for images larger than one cluster).
 int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
-                     bool async_alloc, ResidentPrepared *R);
+                     bool async_alloc, ResidentPrepared *R, int strips = 0);
 cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream);
 int resident_collect(const ResidentPrepared &R, const thin_options &opt, cudaStream_t stream, thin_stats *out);
 void resident_release(ResidentPrepared &R, cudaStream_t stream);
@@ -106,6 +116,10 @@ void resident_release(ResidentPrepared &R, cudaStream_t stream);
 int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, int *rows_out, int *rp_out);
 // Shared memory one block may take when `blocks` blocks share an SM.
 size_t resident_smem_limit(int blocks);
+// Wide mode: the fewest strips (clusters of *c_out blocks of nw warps, the
+// largest cluster size that works) whose shared memory holds the image, all
+// clusters resident at once; 0 if none.
+int resident_wide_strips(int w, int h, int dtype, size_t smem_limit, int nw, int *c_out);
 
 // A tiled launch prepared on the host (opaque; thin_tiled.cu).
 struct TiledPrepared;
@@ -125,9 +139,20 @@ int cuda_status(cudaError_t e);
 struct Grouping {
     int nw = 16;
     std::vector<std::pair<int, std::vector<int>>> resident;
+    struct Wide {
+        int job, strips, C;
+    };
+    std::vector<Wide> wide;  // one wide launch each
     std::vector<int> tiled;
 };
-int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G);
+// allow_wide: large images may take the wide resident mode (a cooperative
+// launch over the whole GPU); serving turns it off so that its lanes share
+// the GPU.
+int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G, bool allow_wide = true);
+
+// thin_batch on validated images (the C-ABI entry without the checks).
+int batch_validated(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out,
+                    bool allow_wide);
 
 // Every launch group of a batch, prepared; enqueue() is device work only
 // (resident groups forked onto up to four side streams with events, joined
@@ -138,6 +163,8 @@ struct Execution {
     bool async = true;
     std::vector<ResidentPrepared> res;
     std::vector<std::vector<int>> res_idx;
+    std::vector<ResidentPrepared> wide;
+    std::vector<int> wide_idx;
     TiledPrepared *tiled = nullptr;
     std::vector<int> tiled_idx;
     int prepare(const std::vector<JobSpec> &specs, const Grouping &G, const thin_options &o, cudaStream_t s,

@@ -39,6 +39,14 @@ namespace {
 // registers a thread either way).
 constexpr int kResMaxWarps = 16;
 constexpr int kResStep = 8;  // phases between halo exchanges = halo rows held from each neighbour
+// A warp with more queued groups than this tests them all first and lowers
+// the few that qualify on packed lanes; with fewer it lowers as it tests.
+// The lowering pass starts from the test pass's result (one byte per group),
+// and the common mode (lambda-thinning, F^- = max, (8,4)) has its own build
+// of the point test.
+constexpr int kTwoPass = 32;
+constexpr bool kOkPass = true;
+constexpr bool kFix = true;
 
 __device__ const PointTable d_res_point_table = kPointTable;
 __device__ const PointTable d_res_component_table = kComponentTable;
@@ -57,6 +65,7 @@ struct Ctrl {
     unsigned long long nlow;
     unsigned long long ntest;
     long long peer_last[8];  // every block's `last`, pushed by the blocks themselves each phase
+    int bar_ok;              // result of the last grid barrier (wide launches)
 };
 
 __host__ __device__ inline size_t res_bits_off(int rows, int rp) { return (kOffRows + size_t(rows) * rp + 15) / 16 * 16; }
@@ -76,7 +85,8 @@ __host__ __device__ inline int res_warp_queue(int rows, int wpr, int nw)
 }
 __host__ __device__ inline size_t res_smem_bytes(int rows, int rp, int wpr, int nw)
 {
-    return res_queue_off(rows, rp, wpr) + size_t(2) * nw * res_warp_queue(rows, wpr, nw) + 16;
+    // per warp: 16-bit group codes, then one byte per group (its test result)
+    return res_queue_off(rows, rp, wpr) + size_t(3) * nw * res_warp_queue(rows, wpr, nw) + 16;
 }
 
 __device__ __forceinline__ unsigned long long res_gtimer()
@@ -104,6 +114,44 @@ __device__ bool res_mbar_wait(uint32_t bar, uint32_t parity, unsigned long long 
         if (ok) return true;
         if (res_gtimer() - t0 > timeout_ns) return false;
     }
+}
+
+// Barrier over all blocks of a wide launch, with a time limit: false if the
+// wait ran out (THIN_ERR_TIMEOUT posted) or another block posted an error.
+__device__ bool res_grid_barrier(ResCtl *ctl, unsigned nblocks, unsigned long long timeout_ns, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctl->bar_gen;
+        volatile int *err = &ctl->error;
+        const unsigned g0 = *gen;
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = res_gtimer();
+            while (*gen == g0) {
+                if (*err) {
+                    ok = 0;
+                    break;
+                }
+                if (res_gtimer() - t0 > timeout_ns) {
+                    atomicCAS(&ctl->error, 0, THIN_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*err) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 // Marks, in the dirty bitmap `bm` of one parity, the group in cell row cr,
@@ -154,12 +202,23 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
     uint32_t bar_parity = 0;
     __syncthreads();
 
-    for (;;) {
-        if (rank == 0 && tid == 0) ctrl->job = int(atomicAdd(&P.ctl->next_job, 1u));
-        cluster.sync();
-        const int job = cluster.map_shared_rank(ctrl, 0)->job;
-        cluster.sync();  // every block has read the leader's word before it may leave or overwrite it
-        if (job >= P.njobs) break;
+    const bool wide = P.strips > 0;
+    const int S = wide ? P.strips : 1;                  // strips of the image (clusters)
+    const int strip = wide ? int(blockIdx.x) / C : 0;   // this cluster's strip
+    const int gb = strip * C + rank;                    // block index within the image
+    const int B = S * C;                                // blocks per image
+    for (int iter = 0;; ++iter) {
+        int job;
+        if (wide) {
+            if (iter > 0) break;  // a wide launch runs its one image
+            job = 0;
+        } else {
+            if (rank == 0 && tid == 0) ctrl->job = int(atomicAdd(&P.ctl->next_job, 1u));
+            cluster.sync();
+            job = cluster.map_shared_rank(ctrl, 0)->job;
+            cluster.sync();  // every block has read the leader's word before it may leave or overwrite it
+            if (job >= P.njobs) break;
+        }
         const ResJob J = P.jobs[job];
         const int es = J.dtype == THIN_U16 ? 2 : 1;
         const int mode = P.rule | (J.adj << 2);      // F^- reading, operator, adjacency pair
@@ -175,7 +234,8 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         uint32_t *dirty = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
         const int WQ = res_warp_queue(LR, WPR, NW);
         uint16_t *wqueue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR)) + warp * WQ;
-        const int row0 = rank * R;       // first own image row
+        uint8_t *wok = smem + res_queue_off(LR, RP, WPR) + size_t(2) * NW * WQ + size_t(warp) * WQ;
+        const int row0 = gb * R;         // first own image row
         const int ybase = row0 - HR;     // image row of shared row 0
         const int rowb = J.w * es;
         const char *gimg = reinterpret_cast<const char *>(J.img);
@@ -223,6 +283,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         const uint32_t *comp = tabs + 256;
 
         long long g = P.start_phase;
+        long long steps = 0;
         int converged = 0;
         int nlow = 0, ntest = 0;
         for (;;) {  // steps of H phases between exchanges of halo rows
@@ -236,7 +297,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                 uint32_t *d_col = dirty + (2 * (py ^ 1) + px) * slot_words;   // rows above and below
                 uint32_t *d_diag = dirty + (2 * (py ^ 1) + (px ^ 1)) * slot_words;
                 // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
-                const int rr = C > 1 ? Hs - 1 - j : 0;
+                const int rr = B > 1 ? Hs - 1 - j : 0;
                 const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
                 // the groups of the other three parities next to a moved point become dirty
                 auto mark = [&](int cr, int cc, uint32_t moved) {
@@ -303,7 +364,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                     }
                     __syncwarp();
                     int nl = nq;
-                    if (!simd || nq > 32) {
+                    if (!simd || nq > kTwoPass) {
                         // test first; the groups that lower are packed to the front of the queue
                         // (in place: a chunk's slots are read before any of them is written)
                         nl = 0;
@@ -319,7 +380,11 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                 ntest += __popc(in);
                                 uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
                                 if (simd) {
-                                    lowers = test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode) != 0;
+                                    const uint32_t okb = (kFix && mode == 0)
+                                                             ? test_u8<0>(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode)
+                                                             : test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode);
+                                    lowers = okb != 0;
+                                    code |= int((okb | (okb >> 7) | (okb >> 14) | (okb >> 21)) & 0xfu) << 16;
                                 } else {
                                     const uint32_t moved =
                                         es == 2 ? item_table<uint16_t>(reinterpret_cast<const uint16_t *>(rb - RP),
@@ -335,7 +400,11 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                 }
                             }
                             const unsigned bal = __ballot_sync(0xffffffffu, lowers);
-                            if (lowers) wqueue[nl + __popc(bal & ((1u << lane) - 1u))] = uint16_t(code);
+                            if (lowers) {
+                                const int at = nl + __popc(bal & ((1u << lane) - 1u));
+                                wqueue[at] = uint16_t(code);
+                                wok[at] = uint8_t(code >> 16);  // which of the four points passed the test
+                            }
                             nl += __popc(bal);
                         }
                         __syncwarp();
@@ -347,9 +416,20 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                         int gcr, gcc;
                         uint32_t vm, in;
                         where(code, gcr, gcc, vm, in);
-                        if (nq <= 32) ntest += __popc(in);
+                        if (nq <= kTwoPass) ntest += __popc(in);
                         uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
-                        const uint32_t moved = item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
+                        uint32_t moved;
+                        if (kOkPass && nq > kTwoPass) {  // tested in the first pass: start lowering at once
+                            const uint32_t o4 = wok[k];
+                            const uint32_t okb = (o4 & 1u) | ((o4 & 2u) << 7) | ((o4 & 4u) << 14) | ((o4 & 8u) << 21);
+                            moved = (kFix && mode == 0)
+                                        ? item_u8_tested<0>(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow)
+                                        : item_u8_tested(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow);
+                        } else {
+                            moved = (kFix && mode == 0)
+                                        ? item_u8<0>(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow)
+                                        : item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
+                        }
                         if (moved) {
                             mark(gcr, gcc, moved);
                             if (moved & in) moved_own = true;
@@ -361,49 +441,96 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             }
             // ---- end of a step: every block's last change, then the stop test
             __syncthreads();
-            if (tid < C) cluster.map_shared_rank(ctrl, tid)->peer_last[rank] = ctrl->last;  // push to every block
-            cluster.sync();
+            const int sp = int(steps & 1);  // buffer of this step in the exchange snapshot
+            ++steps;
             long long lc = -1;
-            for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+            if (wide) {
+                // boundary rows (and their dirty bits) for the neighbouring strips go to a global
+                // snapshot; a grid barrier; then every block reads the global last change
+                const int vrow = RP / 16;
+                const int dwords = 4 * (HC + 1) * WPR;
+                auto publish = [&](int side, int row_from, int cell_from) {
+                    unsigned char *slot = P.xbuf + ((size_t(gb) * 2 + side) * 2 + sp) * P.xslot;
+                    uint4 *dst = reinterpret_cast<uint4 *>(slot);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(rows_base + size_t(row_from) * RP);
+                    for (int e = tid; e < HR * vrow; e += blockDim.x) __stcg(dst + e, src[e]);
+                    uint32_t *dd = reinterpret_cast<uint32_t *>(slot + size_t(HR) * RP);
+                    for (int e = tid; e < dwords; e += blockDim.x) {
+                        const int q = e / ((HC + 1) * WPR), o = e - q * (HC + 1) * WPR;
+                        __stcg(dd + e, dirty[q * slot_words + cell_from * WPR + o]);
+                    }
+                };
+                if (rank == 0 && strip > 0) publish(0, HR, HC - 1);              // my first own rows, for the strip above
+                if (rank == C - 1 && strip + 1 < S) publish(1, R, R / 2);        // my last own rows, for the strip below
+                if (tid == 0) atomicMax(&P.ctl->gl_last, ctrl->last);
+                __threadfence();
+                if (!res_grid_barrier(P.ctl, gridDim.x, P.timeout_ns, &ctrl->bar_ok)) break;
+                lc = *reinterpret_cast<volatile long long *>(&P.ctl->gl_last);
+            } else {
+                if (tid < C) cluster.map_shared_rank(ctrl, tid)->peer_last[rank] = ctrl->last;  // push to every block
+                cluster.sync();
+                for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+            }
             if (g - P.start_phase >= 4 && lc < g - 3) {  // three quiet phases everywhere: fixed point
                 converged = 1;
                 break;
             }
             if (P.max_phases >= 0 && g - P.start_phase >= P.max_phases) break;
-            if (C > 1) {
+            if (B > 1) {
                 // halo rows and their dirty bits from the blocks above and below (their own rows);
                 // the marks a neighbour made on my first or last row (from its own rows, which I
                 // do not follow to the end of a step) are merged into mine
                 const int vrow = RP / 16;
-                if (rank > 0) {
-                    const uint8_t *nrows = cluster.map_shared_rank(rows_base, rank - 1);
-                    const uint32_t *nd = cluster.map_shared_rank(dirty, rank - 1);
-                    const uint4 *src = reinterpret_cast<const uint4 *>(nrows + size_t(R) * RP);
+                if (gb > 0) {
+                    const uint4 *src;
+                    const uint32_t *nd;
+                    int nd_from;  // first cell row to read in nd
+                    if (rank > 0) {
+                        src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank - 1) + size_t(R) * RP);
+                        nd = cluster.map_shared_rank(dirty, rank - 1);
+                        nd_from = R / 2;
+                    } else {  // the strip above published its last rows
+                        const unsigned char *slot = P.xbuf + ((size_t(gb - 1) * 2 + 1) * 2 + sp) * P.xslot;
+                        src = reinterpret_cast<const uint4 *>(slot);
+                        nd = reinterpret_cast<const uint32_t *>(slot + size_t(HR) * RP);
+                        nd_from = -1;
+                    }
                     uint4 *dst = reinterpret_cast<uint4 *>(rows_base);
-                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
+                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = nd_from >= 0 ? src[e] : __ldcg(src + e);
                     for (int e = tid; e < 4 * (HC + 1) * WPR; e += blockDim.x) {
                         // neighbour cell rows R/2 .. R/2 + HC -> mine 0 .. HC
                         const int q = e / ((HC + 1) * WPR), o = e - q * (HC + 1) * WPR;
-                        const uint32_t v = nd[q * slot_words + (R / 2) * WPR + o];
+                        const uint32_t v = nd_from >= 0 ? nd[q * slot_words + nd_from * WPR + o] : __ldcg(nd + e);
                         uint32_t &d = dirty[q * slot_words + o];
                         d = o < (HC - 1) * WPR ? v : (d | v);  // the two cell rows at the seam: both blocks' marks
                     }
                 }
-                if (rank + 1 < C) {
-                    const uint8_t *nrows = cluster.map_shared_rank(rows_base, rank + 1);
-                    const uint32_t *nd = cluster.map_shared_rank(dirty, rank + 1);
-                    const uint4 *src = reinterpret_cast<const uint4 *>(nrows + size_t(HR) * RP);
+                if (gb + 1 < B) {
+                    const uint4 *src;
+                    const uint32_t *nd;
+                    int nd_from;
+                    if (rank + 1 < C) {
+                        src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(rows_base, rank + 1) + size_t(HR) * RP);
+                        nd = cluster.map_shared_rank(dirty, rank + 1);
+                        nd_from = HC - 1;
+                    } else {  // the strip below published its first rows
+                        const unsigned char *slot = P.xbuf + ((size_t(gb + 1) * 2 + 0) * 2 + sp) * P.xslot;
+                        src = reinterpret_cast<const uint4 *>(slot);
+                        nd = reinterpret_cast<const uint32_t *>(slot + size_t(HR) * RP);
+                        nd_from = -1;
+                    }
                     uint4 *dst = reinterpret_cast<uint4 *>(rows_base + size_t(HR + R) * RP);
-                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = src[e];
+                    for (int e = tid; e < HR * vrow; e += blockDim.x) dst[e] = nd_from >= 0 ? src[e] : __ldcg(src + e);
                     for (int e = tid; e < 4 * (HC + 1) * WPR; e += blockDim.x) {
                         // neighbour cell rows HC - 1 .. 2 HC - 1 -> mine HC + R/2 - 1 .. 2 HC + R/2 - 1
                         const int q = e / ((HC + 1) * WPR), o = e - q * (HC + 1) * WPR;
-                        const uint32_t v = nd[q * slot_words + (HC - 1) * WPR + o];
+                        const uint32_t v = nd_from >= 0 ? nd[q * slot_words + nd_from * WPR + o] : __ldcg(nd + e);
                         uint32_t &d = dirty[q * slot_words + (HC + R / 2 - 1) * WPR + o];
                         d = o >= 2 * WPR ? v : (d | v);
                     }
                 }
-                cluster.sync();  // nobody changes its own rows before its neighbours have copied them
+                if (C > 1) cluster.sync();  // nobody changes its own rows before its neighbours have copied them
+                else __syncthreads();
             }
         }
         // ---- results
@@ -430,15 +557,17 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             }
         }
         if (tid == 0) {
-            ResStat &S = P.st[job];
-            atomicAdd(&S.lowered, ctrl->nlow);
-            atomicAdd(&S.tested, ctrl->ntest);
-            if (rank == 0) {
+            ResStat &St = P.st[job];
+            atomicAdd(&St.lowered, ctrl->nlow);
+            atomicAdd(&St.tested, ctrl->ntest);
+            if (gb == 0) {
                 long long lc = -1;
-                for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
-                S.last_change = lc;
-                S.phases = g - P.start_phase;
-                S.converged = converged;
+                if (wide) lc = *reinterpret_cast<volatile long long *>(&P.ctl->gl_last);
+                else
+                    for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+                St.last_change = lc;
+                St.phases = g - P.start_phase;
+                St.converged = converged;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the next bulk copy
@@ -471,22 +600,26 @@ cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
     return e;
 }
 
+// Wide launches are cooperative: the clusters of one image wait on one
+// another at every step, so all of them must be resident at once.
 template <int NW>
 cudaError_t resident_launch(int C, int grid, size_t smem, cudaStream_t stream, const ResArgs &P)
 {
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
     cfg.blockDim = dim3(NW * 32);
     cfg.gridDim = dim3(grid);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = P.strips > 0 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, k_resident<NW>, P);
 }
 
@@ -513,6 +646,49 @@ int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, in
     return 0;
 }
 
+// Wide mode: the largest cluster size C (8, 4, 2, 1) and the fewest strips
+// S (clusters) whose shared memory holds the image with all S clusters
+// resident at once (clusters must fit within a GPC, so large clusters cannot
+// use every SM).  Returns S and stores C, or 0 if none.
+int resident_wide_strips(int w, int h, int dtype, size_t smem_limit, int nw, int *c_out)
+{
+    const int es = dtype == THIN_U16 ? 2 : 1;
+    const int rp = int((size_t(w) * es + 15) / 16 * 16) + 32;
+    const int cw = (w + 7) / 8, wpr = (cw + 31) / 32;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int max_blocks = sms * (kResMaxWarps / nw);
+    for (int C = 8; C >= 1; C /= 2) {
+        for (int S = 2; S * C <= max_blocks; ++S) {
+            int rows = (h + S * C - 1) / (S * C);
+            rows += rows & 1;
+            const int held = rows + 2 * std::min(kResStep, rows);
+            if (held / 2 * cw > 65535) continue;  // queue codes are 16-bit
+            const size_t smem = res_smem_bytes(held, rp, wpr, nw);
+            if (smem > smem_limit) continue;
+            // every cluster of the launch must be resident at once
+            int grid = 0;
+            cudaError_t e;
+            switch (nw) {
+            case 4: e = resident_shape<4>(C, S, smem, &grid); break;
+            case 8: e = resident_shape<8>(C, S, smem, &grid); break;
+            default: e = resident_shape<16>(C, S, smem, &grid); break;
+            }
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            if (grid == S * C) {
+                if (c_out) *c_out = C;
+                return S;
+            }
+            break;  // more strips of this size fit even less: try smaller clusters
+        }
+    }
+    return 0;
+}
+
 // Shared memory a block may take when `blocks` blocks share an SM.
 size_t resident_smem_limit(int blocks)
 {
@@ -529,13 +705,16 @@ size_t resident_smem_limit(int blocks)
 // Host-side preparation of one launch: job table (longest first), stats and
 // control words, and their pristine copies, all in one device allocation.
 int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
-                     bool async_alloc, ResidentPrepared *R)
+                     bool async_alloc, ResidentPrepared *R, int strips)
 {
     *R = ResidentPrepared();
     R->n = n;
     R->C = C;
     R->nw = nw;
+    R->strips = strips;
     R->async_alloc = async_alloc;
+    if (strips > 0 && n != 1) return THIN_ERR_ARG;  // a wide launch runs one image
+    const int B = strips > 0 ? strips * C : C;      // blocks per image
     if (nw != 4 && nw != 8 && nw != 16) return THIN_ERR_ARG;
     const size_t limit = resident_smem_limit(kResMaxWarps / nw);
     std::vector<ResJob> rj(n);
@@ -551,12 +730,12 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
         r.h = J.h;
         r.dtype = J.dtype;
         r.lam = J.lam;
-        int rows = (J.h + C - 1) / C;
+        int rows = (J.h + B - 1) / B;
         rows += rows & 1;
         r.rows = rows;
         // halo rows must be own rows of the neighbouring block: never deeper than a block's share
         r.steph = std::min(kResStep, rows);
-        r.hr = C > 1 ? r.steph : 0;
+        r.hr = B > 1 ? r.steph : 0;
         r.rp = int((size_t(J.w) * es + 15) / 16 * 16) + 32;
         r.cw = (J.w + 7) / 8;
         r.wpr = (r.cw + 31) / 32;
@@ -586,7 +765,14 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     const size_t o_ctl = o_st + st_bytes;
     const size_t o_st0 = o_ctl + 256;
     const size_t o_ctl0 = o_st0 + st_bytes;
-    const size_t total = o_ctl0 + 256;
+    // wide: per block, 2 sides x 2 step parities of (halo rows + their dirty words)
+    size_t xslot = 0;
+    if (strips > 0) {
+        const ResJob &r = rj[0];
+        xslot = (size_t(r.hr) * r.rp + size_t(4) * (r.hr / 2 + 1) * r.wpr * 4 + 255) / 256 * 256;
+    }
+    const size_t o_x = o_ctl0 + 256;
+    const size_t total = o_x + xslot * 4 * size_t(B);
     cudaError_t e = async_alloc ? cudaMallocAsync(reinterpret_cast<void **>(&R->base), total, stream)
                                 : cudaMalloc(reinterpret_cast<void **>(&R->base), total);
     if (e != cudaSuccess) {
@@ -601,6 +787,7 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     }
     ResCtl ctl0;
     std::memset(&ctl0, 0, sizeof ctl0);
+    ctl0.gl_last = -1;
     e = cudaMemcpyAsync(R->base + o_jobs, sorted.data(), sizeof(ResJob) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_st0, st0.data(), sizeof(ResStat) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_ctl0, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
@@ -618,13 +805,18 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     P.start_phase = opt.start_phase;
     P.max_phases = opt.max_phases;
     P.timeout_ns = 2000000000ull;
+    P.strips = strips;
+    P.xbuf = strips > 0 ? reinterpret_cast<unsigned char *>(R->base + o_x) : nullptr;
+    P.xslot = xslot;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
     if (e == cudaSuccess) {
+        const int want = strips > 0 ? strips : n;  // clusters wanted
         switch (nw) {
-        case 4: e = resident_shape<4>(C, n, smem, &R->grid); break;
-        case 8: e = resident_shape<8>(C, n, smem, &R->grid); break;
-        default: e = resident_shape<16>(C, n, smem, &R->grid); break;
+        case 4: e = resident_shape<4>(C, want, smem, &R->grid); break;
+        case 8: e = resident_shape<8>(C, want, smem, &R->grid); break;
+        default: e = resident_shape<16>(C, want, smem, &R->grid); break;
         }
+        if (e == cudaSuccess && strips > 0 && R->grid < B) return THIN_ERR_ARG;  // not all strips fit at once
     }
     return e == cudaSuccess ? THIN_OK : cuda_status(e);
 }

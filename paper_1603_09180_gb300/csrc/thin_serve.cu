@@ -154,7 +154,6 @@ void lane_main(thin_server *S)
         stream = nullptr;
     }
     std::vector<Req *> batch;
-    std::vector<thin_job> jobs;
     std::vector<thin_stats> st;
     for (;;) {
         batch.clear();
@@ -179,7 +178,7 @@ void lane_main(thin_server *S)
         }
         if (batch.empty()) continue;
         // device slots, input copies, one batch, result copies
-        jobs.clear();
+        std::vector<JobSpec> jobs;
         std::vector<Req *> ok;
         for (Req *r : batch) {
             r->rc = THIN_OK;
@@ -191,19 +190,17 @@ void lane_main(thin_server *S)
                 r->rc = cuda_status(e);
                 continue;
             }
-            thin_job j;
-            j.img_dev = r->dev;
-            j.w = r->w;
-            j.h = r->h;
-            j.pitch = r->dpitch;
-            j.dtype = r->dtype;
-            j.lambda = r->lam;
-            jobs.push_back(j);
+            jobs.push_back(JobSpec{r->dev, r->w, r->h, r->dpitch, r->dtype, r->lam, THIN_ADJ_8_4});
             ok.push_back(r);
         }
         st.assign(ok.size(), thin_stats{});
         int rc = THIN_OK;
-        if (!ok.empty()) rc = thin_batch(jobs.data(), int(jobs.size()), THIN_ADJ_8_4, stream, nullptr, st.data());
+        if (!ok.empty()) {
+            // the lanes share the GPU: no wide launch (it would hold every SM for one image)
+            thin_options o;
+            thin_default_options(&o);
+            rc = batch_validated(jobs, o, stream, st.data(), false);
+        }
         for (size_t k = 0; k < ok.size(); ++k) {
             Req *r = ok[k];
             r->st = st[k];

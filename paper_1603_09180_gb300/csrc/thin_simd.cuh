@@ -68,15 +68,47 @@ __device__ __forceinline__ uint32_t merge_dirs(const uint32_t lt[8])
 // an end point (exactly one neighbour >= F(x)) is kept when
 // F(x) - alpha^- > lambda.  Returns 0x01 in the bytes of the points that may
 // be lowered, among those set in `vm`.
-__device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                            uint32_t lam, int mode, uint32_t &M)
+// Lower-neighbour masks of the four points at centre values c (byte k = mask of point k).
+__device__ __forceinline__ uint32_t lower_mask4(uint32_t c, const uint32_t nb[8])
 {
-    const int rule = mode & 1;
     const uint32_t bl = c & 0x7f7f7f7fu, bh = c & kMsb8;
     uint32_t lt[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) lt[d] = lt8(nb[d], c, bl, bh);
-    M = merge_dirs(lt);
+    return merge_dirs(lt);
+}
+
+// alpha^- of the four points given their lower masks M: the largest lower
+// neighbour, by a tree of byte maxima (0 where a mask is empty).
+__device__ __forceinline__ uint32_t alpha4(const uint32_t nb[8], uint32_t M)
+{
+#define THIN_LOWER_NB(d) (nb[d] & ((((M >> (d)) & kLsb8) * 0xffu)))
+    return __vmaxu4(__vmaxu4(__vmaxu4(THIN_LOWER_NB(0), THIN_LOWER_NB(1)), __vmaxu4(THIN_LOWER_NB(2), THIN_LOWER_NB(3))),
+                    __vmaxu4(__vmaxu4(THIN_LOWER_NB(4), THIN_LOWER_NB(5)), __vmaxu4(THIN_LOWER_NB(6), THIN_LOWER_NB(7))));
+#undef THIN_LOWER_NB
+}
+
+// FIX >= 0 fixes the mode word at compile time (the kernels pass the common
+// mode, lambda-thinning with F^- = max, this way); FIX < 0 reads `mode`.
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
+                                             uint32_t lam, int mode, uint32_t M);
+
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
+                                            uint32_t lam, int mode, uint32_t &M)
+{
+    M = lower_mask4(c, nb);
+    return decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
+}
+
+// decide4 with the lower masks M of the centre values c already computed.
+template <int FIX>
+__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
+                                             uint32_t lam, int mode_rt, uint32_t M)
+{
+    const int mode = FIX >= 0 ? FIX : mode_rt;
+    const int rule = mode & 1;
     const uint32_t iso = M & 0xaaaaaaaau & ~rot_prev(M) & ~rot_next(M);
     const uint32_t mc = M ^ iso;                              // counted lower neighbours
     const uint32_t st = mc & ~rot_prev(mc);                   // starts of their runs
@@ -128,6 +160,7 @@ __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], ui
 // the bytes lowered (0x01 each) over all iterations; `c` receives the new
 // values, `nin` the lowering steps of the points also in `in`.  `comp` is the
 // component-mask table.
+template <int FIX = -1>
 __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
                                            const uint32_t *comp, uint32_t lam, int mode, int &nin)
 {
@@ -135,7 +168,7 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
         uint32_t M;
-        const uint32_t ok = decide4(c, nb, vm, comp, lam, mode, M);
+        const uint32_t ok = decide4<FIX>(c, nb, vm, comp, lam, mode, M);
         if (!ok) break;
         // alpha^-: largest lower neighbour, by a tree of byte maxima; direction d
         // of point k is lower iff bit d of byte k of M is set
@@ -148,6 +181,28 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
         c = (alpha & okm) | (c & ~okm);
         okacc |= ok;
         nin += __popc(ok & in);
+    }
+    return okacc;
+}
+
+// lower4 for points whose first test already ran: `ok` holds its result
+// (0x01 per byte that may be lowered at the current values).
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
+                                                  uint32_t ok, const uint32_t *comp, uint32_t lam, int mode, int &nin)
+{
+    uint32_t okacc = 0;
+    uint32_t M = lower_mask4(c, nb);
+#pragma unroll 1
+    for (int it = 0; it < 9; ++it) {
+        if (!ok) break;
+        const uint32_t alpha = alpha4(nb, M);
+        const uint32_t okm = ok * 0xffu;
+        c = (alpha & okm) | (c & ~okm);
+        okacc |= ok;
+        nin += __popc(ok & in);
+        M = lower_mask4(c, nb);
+        ok = decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
     }
     return okacc;
 }
@@ -197,21 +252,43 @@ __device__ __forceinline__ void gather_u8(const uint8_t *ra, const uint8_t *rb, 
 }
 
 // One u8 work item, tested only: 0x01 in the bytes of the points that would be lowered now.
+template <int FIX = -1>
 __device__ __forceinline__ uint32_t test_u8(const uint8_t *ra, const uint8_t *rb, const uint8_t *rc, int px,
                                             uint32_t vm, const uint32_t *comp, uint32_t lam, int mode)
 {
     uint32_t nb[8], c, other, M;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    return decide4(c, nb, vm, comp, lam, mode, M);
+    return decide4<FIX>(c, nb, vm, comp, lam, mode, M);
 }
 
 // One u8 work item, lowered: the lowering loop on its four points, the block written back.
+template <int FIX = -1>
 __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
                                             uint32_t in, const uint32_t *comp, uint32_t lam, int mode, int &nin)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4(c, nb, vm, in, comp, lam, mode, nin);
+    const uint32_t moved = lower4<FIX>(c, nb, vm, in, comp, lam, mode, nin);
+    if (moved) {
+        uint2 out;
+        if (px == 0)
+            out = make_uint2(__byte_perm(c, other, 0x5140), __byte_perm(c, other, 0x7362));
+        else
+            out = make_uint2(__byte_perm(other, c, 0x5140), __byte_perm(other, c, 0x7362));
+        *reinterpret_cast<uint2 *>(rb) = out;
+    }
+    return moved;
+}
+
+// item_u8 for a work item whose first test already ran (result `ok`).
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t item_u8_tested(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px,
+                                                   uint32_t vm, uint32_t in, uint32_t ok, const uint32_t *comp,
+                                                   uint32_t lam, int mode, int &nin)
+{
+    uint32_t nb[8], c, other;
+    gather_u8(ra, rb, rc, px, nb, c, other);
+    const uint32_t moved = lower4_tested<FIX>(c, nb, vm, in, ok, comp, lam, mode, nin);
     if (moved) {
         uint2 out;
         if (px == 0)
