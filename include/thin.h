@@ -92,14 +92,17 @@ typedef enum {
 typedef struct {
     int32_t rule;        /* thin_rule */
     int32_t kernel;      /* thin_kernel */
-    int32_t tile_w;      /* tile width in pixels, 0 = default; multiple of 16, 16..224 */
-    int32_t tile_h;      /* tile height in pixels, 0 = default; 8..240 */
-    int32_t halo;        /* phases per tile visit = halo width, 0 = default; 1..8 */
-    int32_t reserved;
+    int32_t tile_w;      /* tiled engine: tile width in pixels, 0 = default (64); multiple of 16, 16..224 */
+    int32_t tile_h;      /* tiled engine: tile height, 0 = default (32); even, >= 8, tile_h + 2 halo <= 256 */
+    int32_t halo;        /* tiled engine: phases per tile visit = halo width, 0 = default (8); 3..8 when a u16
+                            image is in the call, else 3..16; below min(tile_w, tile_h).  A shape that does not
+                            fit one block's shared memory returns THIN_ERR_ARG */
+    int32_t reserved;    /* 0.  Test hook: 1 makes block 0 of the tiled engine skip its first grid barrier, so
+                            that the bounded wait runs out and the call reports THIN_ERR_TIMEOUT */
     int64_t start_phase; /* global phase index of the first phase (resume), >= 0 */
     int64_t max_phases;  /* stop after this many phases; < 0 = run to stability */
     int32_t op;          /* thin_op */
-    int32_t reserved2;
+    int32_t reserved2;   /* 0 */
 } thin_options;
 
 typedef struct {
@@ -264,10 +267,11 @@ const char *thin_version(void);
  * stream) on the device that is current at thin_serve_create.  submit copies
  * the host image into a pinned host buffer and returns at once with a ticket.
  * An idle lane admits queued requests in arrival order while the slot count
- * and the byte budget allow (a request that does not fit waits at the head of
- * the queue), allocates their device images, copies them in, thins them with
- * one thin_batch call, copies the results back and retires them, returning
- * their bytes and slots.  Host staging is one pinned arena allocated at
+ * and the byte budget allow, at most max_slots / 4 of them (a request that
+ * does not fit waits at the head of the queue).  It allocates their device
+ * images, copies them in, thins them with one thin_batch call (large images
+ * on the tiled engine, never the wide mode, so that the lanes share the GPU),
+ * copies the results back and retires them, returning their bytes and slots.  Host staging is one pinned arena allocated at
  * create (a quarter of the device budget, clamped to 256 MiB .. 4 GiB), so
  * submit makes no CUDA allocation.  Requests that arrive while other batches run are
  * admitted by the next idle lane and run on the device beside them.  Each

@@ -166,7 +166,10 @@ void lane_main(thin_server *S)
                 return S->used + S->queue.front()->charge <= S->budget;
             });
             if (S->stop) break;
-            while (!S->queue.empty() && S->in_flight < S->max_slots && int(batch.size()) < kMaxBatch) {
+            // a lane takes at most its share of the slots, so that under load the other lanes
+            // keep admitting while one lane's batch waits for its slowest image
+            const int share = std::max(1, std::min(kMaxBatch, S->max_slots / kLanes));
+            while (!S->queue.empty() && S->in_flight < S->max_slots && int(batch.size()) < share) {
                 Req *r = S->queue.front();
                 if (S->used + r->charge > S->budget) break;
                 S->queue.pop_front();
