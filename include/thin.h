@@ -75,7 +75,8 @@ typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
 typedef enum { THIN_OP_THINNING = 0, THIN_OP_SKELETON = 1 } thin_op;
 
 /* Kernel family.  RESIDENT holds each image in shared memory for its whole
- * run: in one thread-block cluster (images up to about 1.7 MB), or, in the
+ * run: in one thread-block cluster (images up to about 1.25 MB: 1120 x 1120
+ * u8, 816 x 816 u16), or, in the
  * wide mode, in several clusters of one cooperative launch (one block per SM,
  * clusters of 8, 4, 2 or 1 blocks, whichever lets every strip be resident)
  * that exchange boundary rows every 8 phases: images up to about 30 MB.  TILED streams 64 x 32 tiles through shared memory (any
@@ -167,7 +168,10 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
  * thin_plan_create does all host work of a thin_batch call once (checks,
  * launch groups, device job tables, tensor maps) and captures the device
  * work of one run into a CUDA graph: per-run resets, the resident engine's
- * launch groups side by side, the tiled engine after them.
+ * launch groups side by side, the tiled engine after them.  Images that go
+ * to the tiled engine get a tile shape and halo depth chosen by
+ * thin_autotune on the largest of them, unless opt sets tile_w, tile_h or
+ * halo.
  * thin_plan_launch enqueues that graph: every image is thinned in place, with
  * exactly the result thin_batch gives.  The images must stay at the same
  * device addresses while the plan exists; relaunching thins whatever the
@@ -187,6 +191,10 @@ int thin_plan_launch(thin_plan *p, void *stream);
 /* Waits for stream and writes the stats of the plan's last run, one per job
  * (n entries).  Returns THIN_OK or the first non-OK status, as thin_batch. */
 int thin_plan_stats(thin_plan *p, void *stream, thin_stats *out);
+
+/* The tiled engine's tile shape and halo depth the plan chose by autotuning
+ * (all 0 when it has no tiled images or the caller fixed them). */
+int thin_plan_tiling(const thin_plan *p, int *tile_w, int *tile_h, int *halo);
 
 /* Waits for the device to be idle, then frees the plan. */
 int thin_plan_destroy(thin_plan *p);

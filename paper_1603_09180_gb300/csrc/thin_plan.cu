@@ -2,7 +2,8 @@
 // many times as one CUDA graph.
 //
 // thin_plan_create does all host work of thin_batch once: argument checks,
-// launch groups, device job tables, tensor maps, occupancy queries.  It then
+// launch groups, the tiled group's autotuned tile shape and halo, device job
+// tables, tensor maps, occupancy queries.  It then
 // captures the device work of one run -- per-run resets, the resident groups
 // forked onto side streams, the tiled group after them -- into a CUDA graph.
 // thin_plan_launch is one cudaGraphLaunch.
@@ -18,6 +19,7 @@ struct thin_plan {
     std::vector<int> where;             // specs[k] is the caller's job where[k]
     int n = 0;                          // the caller's job count
     thin_options opt;
+    int tile_w = 0, tile_h = 0, halo = 0;  // the tiled group's shape, when autotuned
     bool idle = false;                  // nothing runs (no image with an interior, or max_phases == 0)
     thin::Execution X;
     cudaGraph_t graph = nullptr;
@@ -95,8 +97,27 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
     for (auto &x : ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    // The tiled group's tile shape and halo depth: autotuned on its largest
+    // image (trials on a scratch copy, 64 phases each) unless the caller set them.
+    thin_options ot = o;
+    if (e == cudaSuccess && !G.tiled.empty() && o.tile_w == 0 && o.tile_h == 0 && o.halo == 0) {
+        int big = G.tiled[0];
+        for (int k : G.tiled)
+            if (double(p->specs[k].w) * p->specs[k].h > double(p->specs[big].w) * p->specs[big].h) big = k;
+        const JobSpec &J = p->specs[big];
+        thin_options tuned = o;
+        if (thin_autotune(J.img, J.w, J.h, J.pitch, thin_dtype(J.dtype), J.lam, cs, 64, &tuned, nullptr) == THIN_OK) {
+            // a u16 image in the group caps the halo at 8; autotune tried that image's dtype only
+            bool any16 = false;
+            for (int k : G.tiled) any16 |= p->specs[k].dtype == THIN_U16;
+            if (!any16 || tuned.halo <= 8) ot = tuned;
+        }
+        p->tile_w = ot.tile_w;
+        p->tile_h = ot.tile_h;
+        p->halo = ot.halo;
+    }
     if (e == cudaSuccess) {
-        rc = p->X.prepare(p->specs, G, o, cs, false);  // plan-owned device memory (cudaMalloc)
+        rc = p->X.prepare(p->specs, G, ot, cs, false);  // plan-owned device memory (cudaMalloc)
         if (rc == THIN_OK) e = cudaStreamSynchronize(cs);  // tables uploaded before capture
         if (rc == THIN_OK && e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (rc == THIN_OK && e == cudaSuccess) {
@@ -149,6 +170,15 @@ int thin_plan_stats(thin_plan *p, void *stream, thin_stats *out)
     const int rc = p->X.collect(static_cast<cudaStream_t>(stream), st.data());
     for (size_t k = 0; k < st.size(); ++k) out[p->where[k]] = st[k];
     return rc;
+}
+
+int thin_plan_tiling(const thin_plan *p, int *tile_w, int *tile_h, int *halo)
+{
+    if (!p || !tile_w || !tile_h || !halo) return THIN_ERR_ARG;
+    *tile_w = p->tile_w;
+    *tile_h = p->tile_h;
+    *halo = p->halo;
+    return THIN_OK;
 }
 
 int thin_plan_destroy(thin_plan *p)

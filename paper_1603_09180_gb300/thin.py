@@ -66,7 +66,7 @@ class Job(ctypes.Structure):
 EXPORTS = ["thin_default_options", "thin_run", "thin_batch", "thin_point_table", "thin_version",
            "thin_serve_create", "thin_serve_submit", "thin_serve_poll", "thin_serve_wait_any",
            "thin_serve_destroy", "thin_run_noalloc", "thin_plan_create", "thin_plan_launch", "thin_plan_stats",
-           "thin_plan_destroy", "thin_autotune", "thin_point_table_adj"]
+           "thin_plan_destroy", "thin_autotune", "thin_point_table_adj", "thin_plan_tiling"]
 
 _lib = None
 
@@ -107,6 +107,9 @@ def load(path: str = LIB_PATH):
     lib.thin_plan_launch.restype = i32
     lib.thin_plan_stats.argtypes = [vp, vp, ctypes.POINTER(Stats)]
     lib.thin_plan_stats.restype = i32
+    lib.thin_plan_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+    lib.thin_plan_tiling.restype = i32
     lib.thin_plan_destroy.argtypes = [vp]
     lib.thin_plan_destroy.restype = i32
     lib.thin_autotune.argtypes = [vp, i32, i32, sz, i32, u32, vp, ctypes.c_int64, ctypes.POINTER(Options),
@@ -366,6 +369,14 @@ class GraphPlan(BatchPlan):
         if stats:
             return [self.stats[k].as_dict() for k in range(self.n)], rc
         return None, rc
+
+    def tiling(self):
+        """(tile_w, tile_h, halo) the plan autotuned for its tiled images, zeros if none."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = load().thin_plan_tiling(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        if rc != THIN_OK:
+            raise ThinError(rc, "thin_plan_tiling")
+        return a.value, b.value, c.value
 
     def close(self):
         if self._h:

@@ -99,3 +99,29 @@ def test_autotune_picks_a_valid_shape_and_leaves_the_image(dt, lam):
     torch.cuda.synchronize()
     ref, rst = oracle.thin(img, lam)
     assert np.array_equal(to_host(t), ref) and st["lowered"] == rst["lowered"]
+
+
+def test_plan_autotunes_its_tiled_images():
+    """A plan whose images go to the tiled engine picks their tile shape and halo
+    by timing (on a scratch copy); the replays stay bit-exact to the oracle."""
+    imgs = [synth.value_noise_image(h, w, "u8", seed=h + w) for h, w in [(300, 420), (257, 190), (64, 700)]]
+    lams = [6, 0, 12]
+    refs = [oracle.thin(a, l) for a, l in zip(imgs, lams)]
+    pristine = [to_dev(a) for a in imgs]
+    work = [p.clone() for p in pristine]
+    plan = thin.GraphPlan(work, lams, kernel="tiled")
+    tw, th, halo = plan.tiling()
+    assert tw % 16 == 0 and tw >= 16 and th >= 8 and 3 <= halo <= 8
+    for t, p in zip(work, pristine):
+        assert torch.equal(t, p)  # the trials did not touch the images
+    for _ in range(2):
+        for t, p in zip(work, pristine):
+            t.copy_(p)
+        sts, rc = plan.run(stats=True)
+        assert rc == 0
+        for t, (ref, rst), st in zip(work, refs, sts):
+            assert np.array_equal(to_host(t), ref) and st["lowered"] == rst["lowered"]
+    fixed = thin.GraphPlan(work, lams, kernel="tiled", tile=(32, 32), halo=5)
+    assert fixed.tiling() == (0, 0, 0)  # the caller's shape is used as given
+    plan.close()
+    fixed.close()
