@@ -320,6 +320,7 @@ void thin_point_table_adj(thin_adj adj, uint32_t out[256])
 int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda, thin_adj adj,
              void *stream, const thin_options *opt, thin_stats *out)
 {
+    NvtxRange nv("thin_run");
     thin_options o;
     thin_default_options(&o);
     if (opt) o = *opt;
@@ -341,6 +342,7 @@ int thin_run(void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uin
 
 int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const thin_options *opt, thin_stats *out)
 {
+    NvtxRange nv("thin_batch");
     thin_options o;
     thin_default_options(&o);
     if (opt) o = *opt;

@@ -6,9 +6,21 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/thin.h"
 
 namespace thin {
+
+// An NVTX range over a C-ABI call, for Nsight Systems timelines.  The NVTX
+// header only forwards to a profiler that is attached; otherwise it costs a
+// branch.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Validated description of one image handed to an engine.
 struct JobSpec {

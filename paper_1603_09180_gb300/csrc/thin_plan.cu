@@ -46,6 +46,7 @@ extern "C" {
 
 int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_options *opt, thin_plan **out)
 {
+    NvtxRange nv("thin_plan_create");
     if (!out) return THIN_ERR_ARG;
     *out = nullptr;
     thin_options o;
@@ -143,6 +144,7 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
 
 int thin_plan_launch(thin_plan *p, void *stream)
 {
+    NvtxRange nv("thin_plan_launch");
     if (!p) return THIN_ERR_ARG;
     if (p->idle) return THIN_OK;
     return cuda_status(cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)));

@@ -180,6 +180,7 @@ void lane_main(thin_server *S)
             }
         }
         if (batch.empty()) continue;
+        NvtxRange nv("thin_serve batch");
         // device slots, input copies, one batch, result copies
         std::vector<JobSpec> jobs;
         std::vector<Req *> ok;

@@ -30,6 +30,7 @@ using namespace thin;
 extern "C" int thin_autotune(const void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
                              void *stream, int64_t trial_phases, thin_options *opt, float *best_ms)
 {
+    NvtxRange nv("thin_autotune");
     if (!opt) return THIN_ERR_ARG;
     if (w < 3 || h < 3 || !img_dev || (dt != THIN_U8 && dt != THIN_U16)) return THIN_ERR_ARG;
     const size_t es = elem_size(dt);
