@@ -111,8 +111,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else None
+        self.path = os.environ.get("THIN_BENCH_CLOCKS_CSV")  # optional: keep the raw samples in this file
 
     def __enter__(self):
         try:
