@@ -8,16 +8,20 @@
  * F(x) - F^-(c) <= lambda) is lowered to alpha^-(x, F), the largest value among
  * its strictly lower 8-neighbours (Sec. 2.1), repeatedly until no such point
  * remains (the lowering loop of Sec. 2.2, with lambda-destructible points in
- * place of lambda-deletable, non-lambda-end ones).
+ * place of lambda-deletable, non-lambda-end ones).  The paper's own
+ * lambda-skeleton is selected with thin_options.op.
  *
  * The order of lowering is fixed so that the result is unique: a 2x2-parity
  * subfield schedule.  Phase g (a global phase index, 0, 1, 2, ...) visits the
  * interior points with 2*(y & 1) + (x & 1) == g mod 4; such points are
  * pairwise not 8-adjacent, so a phase equals any sequential order over its
  * points.  Within its phase a point is lowered until it is no longer
- * lambda-destructible.  The run stops once four consecutive phases change
- * nothing.  Border pixels (x = 0, x = w-1, y = 0, y = h-1) are read as
- * neighbours and never written.
+ * lambda-destructible.  The run stops at the schedule's fixed point: three
+ * phases in a row that change nothing mean every point has been tested since
+ * its neighbours last moved.  The engines check this every few phases, so
+ * stats.phases may run a few phases past stats.last_change_phase + 3.  Border
+ * pixels (x = 0, x = w-1, y = 0, y = h-1) are read as neighbours and never
+ * written.
  *
  * Layout: an image is h rows of w pixels, row-major, rows `pitch_bytes` apart;
  * pixel (x, y) is column x of row y.  u8 images hold uint8_t, u16 images
@@ -51,8 +55,9 @@ extern "C" {
 #define THIN_ERR_NOT_CONVERGED (-4) /* stopped by max_phases before stability */
 #define THIN_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
 #define THIN_ERR_CUDA (-6)          /* a CUDA runtime call failed */
-#define THIN_EAGAIN (-7)            /* serving: over the memory budget and the queue is full */
-#define THIN_ERR_TOO_LARGE (-8)     /* thin_run_noalloc: the image needs more than its fixed scratch */
+#define THIN_EAGAIN (-7)            /* serving: the admission queue or the pinned staging is full; retry */
+#define THIN_ERR_TOO_LARGE (-8)     /* thin_run_noalloc: the image needs more than its fixed scratch;
+                                       serving: the image alone exceeds the budget or the staging */
 
 typedef enum { THIN_U8 = 0, THIN_U16 = 1 } thin_dtype;
 /* Adjacency pair (n, nbar) of Sec. 2.1: (8,4) or (4,8).  Under (4,8), T+
