@@ -511,3 +511,24 @@ def test_48_invariants_and_topology(lam):
         assert oracle.level_topology(out, levels, adj=A48) == oracle.level_topology(img, levels, adj=A48)
     # the two adjacency pairs are different operators on this image
     assert not np.array_equal(out, oracle.thin(img, lam)[0])
+
+
+def test_golden_skeleton_and_48_cases():
+    """Hand-worked 3x3 cases (tests/golden/skeleton_and_48_cases.json): the
+    connectivity numbers under both pairs, whether the centre may be lowered,
+    and its final value, for both operators."""
+    doc = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "skeleton_and_48_cases.json")))
+    adjs = {"8,4": oracle.ADJ_8_4, "4,8": oracle.ADJ_4_8}
+    ops = {"thinning": oracle.OP_THIN, "skeleton": oracle.OP_SKELETON}
+    assert len(doc["cases"]) >= 4
+    for c in doc["cases"]:
+        g = np.array(c["grid"])
+        nb, ctr = bf.ring_values(g), int(g[1, 1])
+        m = sum(1 << i for i, v in enumerate(nb) if v < ctr)
+        for a, e in c["expect"].items():
+            assert oracle.mask_numbers(m, adj=adjs[a])[:2] == (e["tplus"], e["tminus"]), (c["name"], a)
+        for chk in c["checks"]:
+            ok, _ = oracle.lowerable(nb, ctr, chk["lam"], op=ops[chk["op"]], adj=adjs[chk["adj"]])
+            assert ok == chk["first"], (c["name"], chk)
+            out, _ = oracle.thin(g.astype(np.int32), chk["lam"], op=ops[chk["op"]], adj=adjs[chk["adj"]])
+            assert out[1, 1] == chk["final"], (c["name"], chk)
