@@ -130,3 +130,38 @@ def test_plan_host_side_errors(lib):
     assert lib.thin_plan_create(jobs, 1, thin.ADJ_8_4, ctypes.byref(o), ctypes.byref(h)) == thin.THIN_ERR_ARG
     assert lib.thin_plan_launch(None, None) == thin.THIN_ERR_ARG
     assert lib.thin_plan_destroy(None) == thin.THIN_ERR_ARG
+
+
+def test_calls_without_work_need_no_device(lib):
+    """Zero images, empty images and images without interior points finish on
+    the host: converged stats, nothing launched (this machine may have no GPU)."""
+    o = thin.options()
+    st = thin.Stats()
+    assert lib.thin_batch(None, 0, thin.ADJ_8_4, None, ctypes.byref(o), None) == thin.THIN_OK
+    assert lib.thin_run(None, 0, 0, 0, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(o), ctypes.byref(st)) == thin.THIN_OK
+    assert st.converged == 1 and st.phases == 0 and st.last_change_phase == -1
+    st = thin.Stats()
+    assert lib.thin_run(ctypes.c_void_p(4096), 9, 2, 9, thin.U8, 0, thin.ADJ_4_8, None, ctypes.byref(o),
+                        ctypes.byref(st)) == thin.THIN_OK
+    assert st.converged == 1
+    assert lib.thin_run_noalloc(None, 0, 0, 0, thin.U8, 0, thin.ADJ_8_4, None, None, ctypes.byref(st)) == thin.THIN_OK
+    h = ctypes.c_void_p()
+    assert lib.thin_plan_create(None, 0, thin.ADJ_8_4, ctypes.byref(o), ctypes.byref(h)) == thin.THIN_OK
+    assert lib.thin_plan_launch(h, None) == thin.THIN_OK
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lib.thin_plan_tiling(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == thin.THIN_OK
+    assert (a.value, b.value, c.value) == (0, 0, 0)
+    assert lib.thin_plan_destroy(h) == thin.THIN_OK
+
+
+def test_option_checks(lib):
+    img = ctypes.c_void_p(4096)
+    for field, bad in (("rule", 2), ("op", 7), ("kernel", 9), ("start_phase", -1), ("tile_w", -16), ("halo", -1)):
+        o = thin.options()
+        setattr(o, field, bad)
+        assert lib.thin_run(img, 9, 9, 9, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(o), None) == thin.THIN_ERR_ARG, field
+    o = thin.options()
+    assert lib.thin_run(img, 9, 9, 9, thin.U16, 0, thin.ADJ_8_4, None, ctypes.byref(o), None) == thin.THIN_ERR_ARG  # odd pitch
+    assert lib.thin_run(ctypes.c_void_p(4097), 9, 9, 18, thin.U16, 0, thin.ADJ_8_4, None, ctypes.byref(o),
+                        None) == thin.THIN_ERR_ARG  # odd address for u16
+    assert lib.thin_run(img, 9, 9, 8, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(o), None) == thin.THIN_ERR_ARG  # pitch < w
