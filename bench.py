@@ -54,9 +54,15 @@ KERNEL_SOURCES = ("thin_resident.cu", "thin_simd.cuh", "thin_common.cuh", "thin_
 
 
 def kernel_source_hash() -> str:
+    """Hash of the dominant kernel's sources with comments and blank space removed
+    (edits to comments keep the recorded counters valid)."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(CSRC, f), "rb").read())
+        src = open(os.path.join(CSRC, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).encode())
     return h.hexdigest()[:16]
 
 

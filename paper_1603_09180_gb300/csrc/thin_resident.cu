@@ -1,22 +1,36 @@
 // thin_resident.cu -- the resident lambda-thinning engine: each image lives
-// in the shared memory of one thread-block cluster for its whole run.
+// in shared memory for its whole run.
 //
-// Block r of a cluster of C blocks holds image rows [r R, r R + R); a point
-// on the first or last of its rows reads the neighbouring row straight from
-// the next block's shared memory (distributed shared memory).  A phase only
-// writes rows of its own parity, and its points read only rows of the other
-// parity, so these reads never race; a cluster barrier ends every phase.
-// Clusters take images from a device-wide counter, so images of different
-// lengths run side by side without any grid-wide synchronisation.
+// Layout.  Block r of a cluster of C blocks holds image rows [r R, r R + R)
+// plus 8 halo rows of each neighbouring block, 16-byte padded.  A block runs 8
+// phases on its own (the exact region shrinks by one row per phase into the
+// halo), then copies fresh halo rows, and their dirty bits, from its
+// neighbours' shared memory (distributed shared memory) between two cluster
+// barriers.  A phase writes only points of its own parity and reads only the
+// other parities, so the blocks of a cluster never race inside a phase.
+// Clusters take images from a device-wide counter, longest first, so images
+// of different lengths run side by side without grid-wide synchronisation.
 //
-// Which points a phase tests.  Each block keeps, per cell of 8 x 2 pixels, a
-// bit "lowered a point in phase g" for the last four phases (four rotating
-// bitmaps).  Phase g tests the 4-point group of a cell only if a cell of its
-// 3 x 3 cell neighbourhood changed in phases g-3 .. g-1: a point none of whose
-// neighbours moved since its own last test cannot have become
-// lambda-destructible.  The first four phases of a run test everything.  The
-// run stops once three phases in a row changed nothing (the image is then at
-// the fixed point of the schedule) or at the phase cap.
+// Which points a phase tests.  Per parity there is one bitmap with a bit per
+// 4-point group (8 x 2 cell): "a neighbour of one of its points moved since
+// the group's last test".  A group that lowers a point sets the bits of the
+// groups of the other three parities around it; a phase consumes its own
+// parity's bits.  A point none of whose neighbours moved since its last test
+// cannot have become lowerable, so the skipped tests change nothing.  Every
+// bit is set at the start of a run.  The run stops once three phases in a row
+// changed nothing anywhere in the image (its fixed point under the schedule)
+// or at the phase cap.
+//
+// Work in a phase.  Each warp scans its share of the parity's bitmap words and
+// queues the groups it finds.  With more than 32 queued groups it tests them
+// all first, packing those that lower (with their test result) to the front of
+// its queue, then lowers them on full lanes starting from that result; with
+// fewer it tests and lowers in one pass.  One block barrier ends the phase.
+//
+// Wide mode.  An image too large for one cluster is spread over all clusters
+// of one cooperative launch, a strip each.  Halo rows cross between clusters
+// through a global snapshot, and a bounded grid barrier every 8 phases
+// carries the stop test.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
