@@ -1,4 +1,6 @@
-// thin_api.cu -- the C-ABI of libthin.so: argument checks and dispatch.
+// thin_api.cu -- the C-ABI of libthin.so: argument checks, and the dispatch
+// of a batch into launch groups (resident clusters by size, wide launches,
+// the tiled engine) that run side by side where they can.
 #include <cuda_runtime.h>
 
 #include <algorithm>

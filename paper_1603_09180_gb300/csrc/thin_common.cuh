@@ -8,9 +8,12 @@
 //   * two ring points are 4-adjacent iff their positions are cyclically consecutive;
 //   * two ring points are 8-adjacent iff consecutive, or both are 4-neighbours two
 //     positions apart (E-N, N-W, W-S, S-E).
+// Under the pair (n, nbar) = (8,4):
 // T+  = number of 8-components of the neighbours >= F(x)      (Sec. 2.1, n = 8)
 // T-- = number of 4-components of the neighbours <  F(x) that hold a 4-neighbour
 //       of x                                                   (Sec. 2.1, nbar = 4)
+// A second table serves (4,8): T+ counts the 4-components of the neighbours
+// >= F(x) that hold a 4-neighbour of x, T-- the 8-components of the lower ones.
 #pragma once
 
 #include <cstdint>
