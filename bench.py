@@ -163,6 +163,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ GPU leg
 
+def rounds_profile(sts, bins: int = 8) -> dict:
+    """Rounds each job ran up to and including its last change (the quiet phases of the stop rule
+    not counted): their spread, and a histogram in `bins` equal-width bins from 0 to the maximum.
+    A long upper tail is time in which few images keep the engine busy."""
+    r = sorted(s["last_change_phase"] // 4 + 1 for s in sts)
+    if not r:
+        return {"jobs": 0}
+    top = r[-1]
+    width = max(1, -(-top // bins))
+    counts = [0] * bins
+    for v in r:
+        counts[min(bins - 1, v // width)] += 1
+    q = lambda f: r[min(len(r) - 1, int(f * len(r)))]
+    return {"jobs": len(r), "min": r[0], "p50": q(0.5), "p90": q(0.9), "max": top,
+            "mean": round(sum(r) / len(r), 1), "bin_width": width, "hist": counts}
+
+
 def max_over_ranks(vals, world: int, device=None):
     """Element-wise max of a list of floats over all ranks (identity at world 1)."""
     if world <= 1:
@@ -320,6 +337,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "step_ms": {"min": round(min(step_ms), 4), "p50": round(statistics.median(step_ms), 4),
                     "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
                     "max": round(max(step_ms), 4)},
+        "rounds": rounds_profile(sts),
         "engine": args.kernel,
     }
     return line

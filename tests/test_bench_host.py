@@ -62,3 +62,15 @@ def test_reference_arm_contract(monkeypatch):
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     json.dumps(line)
     assert bench.run_reference(type("A", (), {"steps": 1, "warmup": 0})(), 1, 2) is None
+
+
+def test_rounds_profile():
+    sys.path.insert(0, ROOT)
+    import bench
+    # last change in phase -1 (none), 0..3 (round 1), 4 (round 2), 39 (round 10)
+    sts = [{"last_change_phase": p} for p in (-1, 0, 3, 4, 39)]
+    r = bench.rounds_profile(sts, bins=5)
+    assert (r["jobs"], r["min"], r["max"], r["p50"]) == (5, 0, 10, 1)
+    assert r["bin_width"] == 2 and r["hist"] == [3, 1, 0, 0, 1] and sum(r["hist"]) == 5
+    assert bench.rounds_profile([]) == {"jobs": 0}
+    json.dumps(r)
