@@ -157,10 +157,18 @@ typedef struct {
 
 /*
  * Lambda-thin n independent images of any sizes, dtypes and lambdas in one
- * device-driven run (a CUDA graph whose body loops on the device until every
- * image is stable).  Each image gets exactly the result thin_run gives it
- * alone.  opt applies to every image (its start_phase too).  out: array of n
- * stats or NULL.  n == 0 is a no-op.
+ * call.  Images that fit one thread-block cluster's shared memory run on the
+ * resident engine, one launch per cluster size, the launches side by side
+ * on streams forked from `stream` and joined back into it.  Images too large
+ * for a cluster run in the wide resident mode, one launch each, when there
+ * are at most two of them (any number with THIN_KERNEL_RESIDENT); otherwise
+ * they go to one persistent launch of the tiled engine, after the resident
+ * launches.  Every such launch loops on the device until its images are
+ * stable.  THIN_KERNEL_TILED sends every image to the tiled engine;
+ * THIN_KERNEL_NAIVE thins the images one after another, as thin_run does
+ * with that kernel.  Each image gets exactly the result thin_run
+ * gives it alone.  opt applies to every image (its start_phase too).  out:
+ * array of n stats or NULL.  n == 0 is a no-op.
  */
 int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const thin_options *opt,
                thin_stats *out);
