@@ -81,13 +81,14 @@ typedef enum { THIN_OP_THINNING = 0, THIN_OP_SKELETON = 1 } thin_op;
 
 /* Kernel family.  RESIDENT holds each image in shared memory for its whole
  * run: in one thread-block cluster (images up to about 1.25 MB: 1120 x 1120
- * u8, 816 x 816 u16), or, in the
- * wide mode, in several clusters of one cooperative launch (one block per SM,
- * clusters of 8, 4, 2 or 1 blocks, whichever lets every strip be resident)
- * that exchange boundary rows every 8 phases: images up to about 30 MB.  TILED streams 64 x 32 tiles through shared memory (any
- * size).  AUTO picks RESIDENT for images that fit a cluster, the wide mode
- * for up to two larger images in a call, and TILED for the rest.  NAIVE runs
- * one launch per phase straight from global memory (the reference slice). */
+ * u8, 816 x 816 u16), or, in the wide mode, in several clusters of one
+ * cooperative launch (one block per SM, clusters of 8, 4, 2 or 1 blocks,
+ * whichever lets every strip be resident) that exchange boundary rows every
+ * 8 phases: images up to about 30 MB.  TILED streams 64 x 32 tiles through
+ * shared memory (any size).  AUTO picks RESIDENT for images that fit a
+ * cluster, the wide mode for up to two larger images in a call, and TILED
+ * for the rest.  NAIVE runs one launch per phase straight from global memory
+ * (the reference slice). */
 typedef enum {
     THIN_KERNEL_AUTO = 0,
     THIN_KERNEL_NAIVE = 1,
@@ -217,12 +218,14 @@ int thin_plan_destroy(thin_plan *p);
  * run h phases per tile visit; the paper has no counterpart).  Times every
  * candidate tile shape and halo depth h (phases per visit) on a scratch copy
  * of the image -- the image itself is not changed -- and writes the fastest
- * into opt->tile_w, opt->tile_h and opt->halo (other fields of *opt are kept
- * and used for the trials: rule, start_phase).  trial_phases bounds each
- * trial (< 0: every trial runs to stability).  best_ms (may be NULL)
- * receives the winner's time.  Synchronous.  Candidates: 64x32 (h 8, 6, 4),
- * 128x32, 64x64, 128x64, 32x32, 96x48, 128x16, 224x32, 48x64 (h 8), 64x16
- * (h 6).  THIN_ERR_ARG for an image without interior points.
+ * into opt->tile_w, opt->tile_h and opt->halo.  The other fields of *opt are
+ * kept and used for the trials (rule, op, start_phase); the trials run under
+ * (8,4) adjacency, whichever pair the image is later thinned with.
+ * trial_phases bounds each trial (< 0: every trial runs to stability).
+ * best_ms (may be NULL) receives the winner's time.  Synchronous.
+ * Candidates: 64x32 (h 8, 6, 4), 128x32, 64x64, 128x64, 32x32, 96x48,
+ * 128x16, 224x32, 48x64 (h 8), 64x16 (h 6).  THIN_ERR_ARG for an image
+ * without interior points.
  */
 int thin_autotune(const void *img_dev, int w, int h, size_t pitch_bytes, thin_dtype dt, uint32_t lambda,
                   void *stream, int64_t trial_phases, thin_options *opt, float *best_ms);
