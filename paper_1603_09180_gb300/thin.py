@@ -168,15 +168,19 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _check_image(img):
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dim() != 2 or (img.numel() and img.stride(1) != 1):
+        raise ValueError("image must be 2-D with unit column stride")
+
+
 def run(img, lam: int, *, rule="max", kernel="auto", tile=None, halo=0, start_phase=0, max_phases=-1,
         stream=None, stats=True, check=True, debug=0, op="thinning", adj=ADJ_8_4):
     """Lambda-thin a CUDA tensor (H x W, uint8/uint16, unit column stride) in place.
 
     Returns the stats dict (stats=True waits for the stream), else None."""
-    if not img.is_cuda:
-        raise ValueError("image must be a CUDA tensor")
-    if img.dim() != 2 or (img.numel() and img.stride(1) != 1):
-        raise ValueError("image must be 2-D with unit column stride")
+    _check_image(img)
     h, w = img.shape
     es = img.element_size()
     pitch = img.stride(0) * es if h > 1 else w * es
@@ -194,16 +198,18 @@ def run(img, lam: int, *, rule="max", kernel="auto", tile=None, halo=0, start_ph
     return rc
 
 
-def autotune(img, lam: int, *, trial_phases: int = -1, rule="max", stream=None):
+def autotune(img, lam: int, *, trial_phases: int = -1, rule="max", op="thinning", stream=None):
     """Best (tile, halo) of the tiled engine for this image (timed on a scratch copy).
 
     Returns ({"tile": (tw, th), "halo": h}, best_ms)."""
+    _check_image(img)
     h, w = img.shape
     es = img.element_size()
-    o = options(rule, KERNEL_TILED)
+    pitch = img.stride(0) * es if h > 1 else w * es
+    o = options(rule, KERNEL_TILED, op=op)
     ms = ctypes.c_float()
-    rc = load().thin_autotune(ctypes.c_void_p(img.data_ptr()), w, h, img.stride(0) * es, _dtype_code(img), int(lam),
-                              _stream_ptr(stream), int(trial_phases), ctypes.byref(o), ctypes.byref(ms))
+    rc = load().thin_autotune(ctypes.c_void_p(img.data_ptr() if img.numel() else 0), w, h, pitch, _dtype_code(img),
+                              int(lam), _stream_ptr(stream), int(trial_phases), ctypes.byref(o), ctypes.byref(ms))
     if rc != THIN_OK:
         raise ThinError(rc, "thin_autotune")
     return {"tile": (o.tile_w, o.tile_h), "halo": o.halo}, ms.value

@@ -165,3 +165,20 @@ def test_option_checks(lib):
     assert lib.thin_run(ctypes.c_void_p(4097), 9, 9, 18, thin.U16, 0, thin.ADJ_8_4, None, ctypes.byref(o),
                         None) == thin.THIN_ERR_ARG  # odd address for u16
     assert lib.thin_run(img, 9, 9, 8, thin.U8, 0, thin.ADJ_8_4, None, ctypes.byref(o), None) == thin.THIN_ERR_ARG  # pitch < w
+
+
+def test_binding_rejects_host_tensors():
+    """The binding marshals CUDA tensors only: a host tensor, a 3-D tensor or a
+    strided column is refused before anything reaches the library."""
+    torch = pytest.importorskip("torch")
+    host = torch.zeros(8, 8, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        thin.run(host, 0)
+    with pytest.raises(ValueError):
+        thin.autotune(host, 0)
+    with pytest.raises(ValueError):
+        thin.batch([host], [0])
+    with pytest.raises(ValueError):
+        thin.BatchPlan([host], [0])
+    with pytest.raises(ValueError):
+        thin.batch([host, host], [0])  # one lambda per image
