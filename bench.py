@@ -5,19 +5,25 @@ at lambda in {0, 5, 20} (192 jobs), in one thin_batch call -- one persistent
 device-driven launch.  Images are restored from pristine device copies and L2
 is flushed (a 512 MiB write) before every timed step, outside the timed
 region.  Timing: CUDA events on the launching stream around each step,
-barrier + synchronize around the K timed steps, max over ranks.
+barrier + synchronize around the K timed steps, max over ranks.  The line
+also carries the metric's other two parts, measured in the same run at N = 1:
+`large` (4096x4096 u8 and 8192x8192 u16 at lambda 0 and 30 through thin_run:
+ms, Gpix-sweeps/s and HBM-roofline fractions) and `serve` (Poisson arrivals
+through the serving API at saturation and at half the measured capacity:
+images/s, p50/p99 latency, and the single-image service time of the mix).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload large|uneven|serve   (the other configurations)
 
---workload large: 4096x4096 u8 and 8192x8192 u16 (values 0..4095) at lambda
-0 and 30 on the tiled engine, with a halo sweep; reports Gpix-sweeps/s and
-the HBM roofline.  --workload uneven: 1024 u8 images with sides log-uniform
-in [64, 2048] and lambda in {0, 10, 25}, one thin_batch call against one
-thin_run call per image.  --workload serve: Poisson arrivals of u8/u16 images
-with sides log-uniform in [128, 4096] through the serving API under a 40 GB
-budget, against a plain one-image-at-a-time path; p50/p99 latency and
-images/s per arrival rate.
+--workload large: the large images with the tiled engine beside the wide
+resident mode and a halo sweep.  --workload uneven: 1024 u8 images with
+sides log-uniform in [64, 2048] and lambda in {0, 10, 25}, one thin_batch
+call against one thin_run call per image.  --workload serve: Poisson
+arrivals of u8/u16 images with sides log-uniform in [128, 4096] through the
+serving API under a 40 GB budget, at 1k..50k requests/s and at 25, 50 and
+90 % of the measured capacity, against a plain one-image-at-a-time path;
+p50/p99 latency and images/s per arrival rate.  Lambda applies to pixel
+values as given, for u8 and u16 alike.
 
 --impl reference times the CPU oracle (the plain sequential subfield
 schedule) on this host's cores over a bounded sample of the same jobs.
@@ -64,6 +70,32 @@ def kernel_source_hash() -> str:
         src = re.sub(r"//[^\n]*", "", src)
         h.update(re.sub(r"\s+", " ", src).encode())
     return h.hexdigest()[:16]
+
+
+ISSUE_FILE = os.path.join(ROOT, "profiles", "roofline_issue.json")
+
+
+def issue_roofline(tested, ms_per_step, peaks):
+    """The resident engine's instruction-issue roofline.  Peak: 152 SMs x 4 schedulers x 1 warp-instruction
+    per clock x the SM clock (MEASURED_PEAKS.json sm_max_mhz).  Achieved: warp-instructions per point test,
+    from an ncu count of smsp__inst_executed.sum over the point tests of the same launch (recorded in
+    profiles/roofline_issue.json for the kernel sources of that hash), times this launch's point tests,
+    over its device time.  None when the record does not match the current sources."""
+    mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak = 152 * 4 * mhz * 1e6
+    try:
+        rec = json.load(open(ISSUE_FILE))
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return {"bound": "alu", "achieved": None, "peak": round(peak / 1e12, 4), "unit": "T warp-instructions/s",
+                "frac": None, "note": "instruction count not recorded for the current kernel sources"}
+    ipt = float(rec["warp_instructions_per_point_test"])
+    achieved = ipt * tested / (ms_per_step / 1e3)
+    return {"bound": "alu", "achieved": round(achieved / 1e12, 4), "peak": round(peak / 1e12, 4),
+            "unit": "T warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions_per_point_test": ipt, "source": "profiles/roofline_issue.json",
+            "peak_derivation": "152 SMs x 4 warp schedulers x 1 warp-instruction/clock x %.0f MHz" % mhz}
 
 
 def workload_images():
@@ -205,6 +237,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     jobs = jobs_of(images)
     n_jobs = len(jobs)
 
+    # inputs of the large-image and serving figures (rank 0, N = 1), made in a spawn pool before any device work
+    extra = rank == 0 and world == 1
+    large_imgs = _gen_pool(large_specs(), 2) if extra and not args.no_large else None
+    serve_pool = serve_lams = None
+    if extra and not args.no_serve:
+        specs, serve_lams = serve_pool_specs(args.serve_pool)
+        serve_pool = _gen_pool(specs, host_cores())
+
     # CPU baseline (rank 0, N = 1 only) before any device work, in a spawn pool
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,7 +316,24 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize(dev)
         if k:  # first one is a warm-up
             e2e_ms.append(e0.elapsed_time(e1))
-    ok = bool(torch.equal(host_out, work.cpu()))
+    copy_ok = bool(torch.equal(host_out, work.cpu()))
+
+    # the other two parts of the metric: large single images (Gpix-sweeps/s against the HBM roofline) and
+    # serving (images/s and p50/p99 latency below and at capacity)
+    large = serve = None
+    if large_imgs is not None:
+        with ClockSampler(local_rank) as clk_l:
+            res_l, peak_l, _ = large_measure(large_imgs, 3, 3, flush, stream)
+        large = {"cases": res_l, "clocks": clk_l.summary(), "steps": 3, "warmup": 3,
+                 "note": "thin_run on the default engine; L2 flushed before every timed run; frac over active "
+                         "pixel-rounds, frac_full over every pixel of every round"}
+    if serve_pool is not None:
+        with ClockSampler(local_rank) as clk_s:
+            serve = serve_summary(serve_pool, serve_lams, dev, args.serve_slots, args.serve_queue, 3.0)
+        serve["clocks"] = clk_s.summary()
+        serve["config"] = ("Poisson arrivals, sides log-uniform [128, 4096], u8/u16 1:1, lambda {0, 10} on pixel "
+                           "values as given, %d-image pool cycled, %d GB budget, %d slots"
+                           % (args.serve_pool, SERVE_BUDGET >> 30, args.serve_slots))
 
     total_ms, e2e_step_ms = max_over_ranks([total_ms, sum(e2e_ms) / len(e2e_ms)], world, dev)
     if rank != 0:
@@ -302,6 +359,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     except Exception:
         pass
     clocks = clk.summary()
+    issue = issue_roofline(pix_rounds, ms_per_step, peaks)
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -327,9 +385,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      "note": "achieved = 2 B x active pixel-rounds (point tests) / thin_batch device time; "
                              "the engine keeps each image in shared memory, so its real limit is instruction "
                              "issue, not HBM (profiles/)"},
+        "roofline_issue": issue,
         "e2e": {"value": round(world * n_jobs / (e2e_step_ms / 1e3), 2), "unit": "images/s",
                 "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(host_out.numel()),
-                "results_checked": ok},
+                "copy_check": copy_ok,
+                "copy_check_note": "the D2H result equals the device result (a check of the copy, not of parity)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -339,6 +399,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                     "max": round(max(step_ms), 4)},
         "rounds": rounds_profile(sts),
         "engine": args.kernel,
+        "large": large,
+        "serve": serve,
     }
     return line
 
@@ -423,58 +485,76 @@ def _timed(fn, restore, flush, stream, steps, warmup):
     return ms
 
 
-def run_large(args):
-    """Large single images on the tiled engine (temporal blocking, active tiles)."""
+LARGE_CASES = [(4096, 4096, "u8", 255, (0, 30)), (8192, 8192, "u16", 4095, (0, 30))]
+
+
+def large_specs():
+    return [(h, w, dt, 1603 + i, vmax) for i, (h, w, dt, vmax, _) in enumerate(LARGE_CASES)]
+
+
+def large_measure(imgs, steps, warmup, flush, stream, compare_tiled=False, halo_sweep=False):
+    """4096^2 u8 and 8192^2 u16 at lambda 0 and 30 on the default engine (thin_run): ms, sweep rates over
+    active and over all pixels, and the HBM roofline (2 sizeof(T) bytes per active pixel-round)."""
     import torch
     from paper_1603_09180_gb300 import thin
+    dev = flush.device
+    peak, src = _peak_hbm()
+    results = []
+    for (h, w, dt, vmax, lams), img in zip(LARGE_CASES, imgs):
+        pristine = _to_dev(img, dev)
+        work = pristine.clone()
+        es = work.element_size()
+        for lam in lams:
+            work.copy_(pristine)
+            st = thin.run(work, lam)  # the default engine: wide resident if the image fits, else tiled
+            engine = "tiled" if st["tiles_visited"] else "resident (wide)"
+            tw, th, H = 64, 32, 8
+            ms = _timed(lambda: thin.run(work, lam, stats=False), lambda: work.copy_(pristine),
+                        flush, stream, steps, warmup)
+            t = statistics.median(ms) / 1e3
+            # pixel-rounds over active tiles (tiled) or tested pixel-rounds (resident: a point is tested
+            # at most once per round, and only while a neighbour moved)
+            active = st["tiles_visited"] * tw * th * H / 4.0 if st["tiles_visited"] else float(st["tested"])
+            full = w * h * st["phases"] / 4.0
+            r = {"image": "%dx%d %s" % (w, h, dt), "lambda": lam, "engine": engine, "ms": round(t * 1e3, 3),
+                 "phases": st["phases"], "tiles_visited": st["tiles_visited"], "tested": st["tested"],
+                 "gpix_sweeps_per_s": round(active / t / 1e9, 2),
+                 "gpix_sweeps_full_per_s": round(full / t / 1e9, 2),
+                 "point_tests_per_s_g": round(st["tested"] / t / 1e9, 2),
+                 "achieved_gbs": round(2 * es * active / t / 1e9, 1),
+                 "frac": round(2 * es * active / t / 1e9 / peak, 4),
+                 "frac_full": round(2 * es * full / t / 1e9 / peak, 4)}
+            if compare_tiled and engine != "tiled":  # the tiled engine on the same image, for comparison
+                ms_t = _timed(lambda: thin.run(work, lam, kernel="tiled", stats=False),
+                              lambda: work.copy_(pristine), flush, stream, max(1, steps // 2), 1)
+                r["tiled_ms"] = round(statistics.median(ms_t), 3)
+            results.append(r)
+        if halo_sweep and dt == "u8":  # the tiled engine's halo depth, 4096^2 u8, lambda 30
+            sweep = {}
+            for H in (3, 4, 6, 8, 12, 16):
+                ms = _timed(lambda: thin.run(work, 30, kernel="tiled", tile=(64, 32) if H <= 8 else (64, 48),
+                                             halo=H, stats=False),
+                            lambda: work.copy_(pristine), flush, stream, 1, 1)
+                sweep[H] = round(ms[0], 3)
+            results[-1]["tiled_halo_sweep_ms"] = sweep
+        del pristine, work
+        torch.cuda.empty_cache()
+    return results, peak, src
+
+
+def run_large(args):
+    """Large single images on the default engine (the wide resident mode or the tiled engine)."""
+    import torch
+    from paper_1603_09180_gb300 import thin
+    imgs = _gen_pool(large_specs(), 2)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     thin.load()
-    cases = [(4096, 4096, "u8", 255, (0, 30)), (8192, 8192, "u16", 4095, (0, 30))]
-    imgs = _gen_pool([(h, w, dt, 1603 + i, vmax) for i, (h, w, dt, vmax, _) in enumerate(cases)], 2)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    peak, src = _peak_hbm()
-    results = []
     with ClockSampler(0) as clk:
-        for (h, w, dt, vmax, lams), img in zip(cases, imgs):
-            pristine = _to_dev(img, dev)
-            work = pristine.clone()
-            es = work.element_size()
-            for lam in lams:
-                work.copy_(pristine)
-                st = thin.run(work, lam)  # the default engine: wide resident if the image fits, else tiled
-                engine = "tiled" if st["tiles_visited"] else "resident (wide)"
-                tw, th, H = 64, 32, 8
-                ms = _timed(lambda: thin.run(work, lam, stats=False), lambda: work.copy_(pristine),
-                            flush, stream, args.steps, args.warmup)
-                t = statistics.median(ms) / 1e3
-                # pixel-rounds over active tiles (tiled) or tested pixel-rounds (resident: a point is tested
-                # at most once per round, and only while a neighbour moved)
-                active = st["tiles_visited"] * tw * th * H / 4.0 if st["tiles_visited"] else float(st["tested"])
-                full = w * h * st["phases"] / 4.0
-                r = {"image": "%dx%d %s" % (w, h, dt), "lambda": lam, "engine": engine, "ms": round(t * 1e3, 3),
-                     "phases": st["phases"], "tiles_visited": st["tiles_visited"], "tested": st["tested"],
-                     "gpix_sweeps_per_s": round(active / t / 1e9, 2),
-                     "gpix_sweeps_full_per_s": round(full / t / 1e9, 2),
-                     "point_tests_per_s_g": round(st["tested"] / t / 1e9, 2),
-                     "achieved_gbs": round(2 * es * active / t / 1e9, 1),
-                     "frac": round(2 * es * active / t / 1e9 / peak, 4)}
-                if engine != "tiled":  # the tiled engine on the same image, for comparison
-                    ms_t = _timed(lambda: thin.run(work, lam, kernel="tiled", stats=False),
-                                  lambda: work.copy_(pristine), flush, stream, max(1, args.steps // 2), 1)
-                    r["tiled_ms"] = round(statistics.median(ms_t), 3)
-                results.append(r)
-            if dt == "u8":  # the tiled engine's halo depth, 4096^2 u8, lambda 30
-                sweep = {}
-                for H in (3, 4, 6, 8, 12, 16):
-                    ms = _timed(lambda: thin.run(work, 30, kernel="tiled", tile=(64, 32) if H <= 8 else (64, 48),
-                                                 halo=H, stats=False),
-                                lambda: work.copy_(pristine), flush, stream, 1, 1)
-                    sweep[H] = round(ms[0], 3)
-                results[-1]["tiled_halo_sweep_ms"] = sweep
-            del pristine, work
-            torch.cuda.empty_cache()
+        results, peak, src = large_measure(imgs, args.steps, args.warmup, flush, stream, compare_tiled=True,
+                                           halo_sweep=True)
     head = results[1]
     return {"metric": "Gpix-sweeps/s (4096^2 u8, lambda 30)", "value": head["gpix_sweeps_per_s"],
             "unit": "Gpix-sweeps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -542,156 +622,213 @@ def run_uneven(args):
             "mpix_per_s": round(px / tb / 1e6, 1), "clocks": clk.summary()}
 
 
+SERVE_BUDGET = 40 << 30
+
+
+def serve_pool_specs(pool_n):
+    from paper_1603_09180_gb300 import synth
+    _, spec0 = synth.serve_trace(1000.0, pool_n)
+    return [(h, w, dt, seed) for h, w, dt, lam, seed in spec0], [lam for h, w, dt, lam, seed in spec0]
+
+
+def _drive(rate, seconds, pool, submit, drain):
+    """Poisson arrivals at `rate` for `seconds` (images cycled from the pool, lambda from the trace,
+    applied to pixel values as given); returns latency and throughput figures."""
+    from paper_1603_09180_gb300 import synth
+    t_arr, spec = synth.serve_trace(rate, int(rate * seconds) + 1, seed=int(rate))
+    sub_t, lat, rejected = {}, [], 0
+    t0 = time.perf_counter()
+    for k, ta in enumerate(t_arr):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        ts = time.perf_counter()
+        tk = submit(pool[k % len(pool)], spec[k][3])
+        if tk is None:
+            rejected += 1
+        else:
+            sub_t[tk] = ts
+    t_sub_end = time.perf_counter()
+    done_t = drain(len(sub_t))
+    for tk, td in done_t.items():
+        lat.append(td - sub_t[tk])
+    t_end = max(done_t.values()) if done_t else t_sub_end
+    # steady state: completions while requests keep arriving, after the first quarter of the window
+    w0 = t0 + 0.25 * (t_sub_end - t0)
+    in_window = sum(1 for td in done_t.values() if w0 <= td <= t_sub_end)
+    lat.sort()
+    pct = lambda q: round(1e3 * lat[min(len(lat) - 1, int(q * len(lat)))], 2) if lat else None
+    return {"rate_per_s": round(rate, 1), "offered": len(t_arr), "completed": len(lat), "rejected": rejected,
+            "images_per_s": round(len(lat) / (t_end - t0), 1),
+            "steady_images_per_s": round(in_window / max(1e-9, t_sub_end - w0), 1),
+            "p50_ms": pct(0.5), "p99_ms": pct(0.99), "seconds": round(t_sub_end - t0, 2)}
+
+
+def serve_served(pool, rate, seconds, slots, queue):
+    """Poisson arrivals through thin_serve_* (continuous batching)."""
+    import threading
+    from paper_1603_09180_gb300 import thin
+    srv = thin.Server(SERVE_BUDGET, max_slots=slots, queue_cap=queue)
+    done_t, errors = {}, []
+    lock = threading.Lock()
+
+    def submit(img, lam):
+        try:
+            return srv.submit(img, lam)
+        except thin.ThinError as e:
+            if e.code == thin.THIN_EAGAIN:
+                return None
+            raise
+
+    def collector(stop):
+        while True:
+            t = srv.wait_any(50)
+            if t is None:
+                if stop.is_set():
+                    return
+                continue
+            td = time.perf_counter()
+            ok, res, st, rc = srv.poll(t)
+            with lock:
+                if ok and rc == 0:
+                    done_t[t] = td
+                else:
+                    errors.append(rc)
+
+    stop = threading.Event()
+    col = threading.Thread(target=collector, args=(stop,), daemon=True)
+    col.start()
+
+    def drain(n):
+        t_lim = time.perf_counter() + 120
+        while time.perf_counter() < t_lim:
+            with lock:
+                if len(done_t) + len(errors) >= n:
+                    break
+            time.sleep(0.002)
+        stop.set()
+        col.join()
+        return dict(done_t)
+
+    r = _drive(rate, seconds, pool, submit, drain)
+    r["errors"] = len(errors)
+    srv.close()
+    return r
+
+
+def serve_plain(pool, rate, seconds, queue, dev):
+    """The plain path at the same arrivals: one worker, one image at a time (H2D, thin_run, D2H)."""
+    import queue as qmod
+    import threading
+    from paper_1603_09180_gb300 import thin
+    q = qmod.Queue(maxsize=queue)
+    done_p, errors_p = {}, []
+    nxt = [0]
+
+    def worker():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            tk, img, lam = item
+            try:
+                t = _to_dev(img, dev)
+                thin.run(t, lam, stats=False)
+                t.cpu()
+                done_p[tk] = time.perf_counter()
+            except Exception:
+                errors_p.append(tk)
+
+    wt = threading.Thread(target=worker, daemon=True)
+    wt.start()
+
+    def submit_p(img, lam):
+        nxt[0] += 1
+        try:
+            q.put_nowait((nxt[0], img, lam))
+            return nxt[0]
+        except qmod.Full:
+            return None
+
+    def drain_p(n):
+        t_lim = time.perf_counter() + 120
+        while len(done_p) + len(errors_p) < n and time.perf_counter() < t_lim:
+            time.sleep(0.002)
+        q.put(None)
+        wt.join(timeout=5)
+        return dict(done_p)
+
+    r = _drive(rate, seconds, pool, submit_p, drain_p)
+    r["errors"] = len(errors_p)
+    return r
+
+
+def service_times_ms(pool, lams, dev):
+    """Each pool image alone, end to end (H2D, thin_run, D2H), wall ms; after one warm-up pass."""
+    import torch
+    from paper_1603_09180_gb300 import thin
+    out = []
+    for rep in range(2):
+        for img, lam in zip(pool, lams):
+            t0 = time.perf_counter()
+            t = _to_dev(img, dev)
+            thin.run(t, lam, stats=False)
+            t.cpu()
+            torch.cuda.synchronize()
+            if rep:
+                out.append(1e3 * (time.perf_counter() - t0))
+    return sorted(out)
+
+
+def serve_summary(pool, lams, dev, slots, queue, seconds):
+    """Serving at saturation (the capacity) and at half of it, with the single-image service time of the
+    mix: the figures the default benchmark line carries."""
+    svc = service_times_ms(pool, lams, dev)
+    sat = serve_served(pool, 20000.0, 2.0, slots, queue)
+    cap = max(1.0, sat["steady_images_per_s"])
+    half = serve_served(pool, 0.5 * cap, max(seconds, min(15.0, 600.0 / (0.5 * cap))), slots, queue)
+    p50svc = round(svc[len(svc) // 2], 2)
+    return {"capacity_images_per_s": cap, "saturated": sat, "at_half_capacity": half,
+            "single_image_service_ms": {"p50": p50svc, "p90": round(svc[int(0.9 * (len(svc) - 1))], 2),
+                                        "max": round(svc[-1], 2)},
+            "p50_over_service_p50_at_half": round(half["p50_ms"] / p50svc, 2) if half["p50_ms"] else None}
+
+
 def run_serve(args):
     """Poisson arrivals through thin_serve_* against a plain one-image-at-a-time path."""
-    import queue
-    import threading
-
-    import numpy as np
     import torch
-    from paper_1603_09180_gb300 import synth, thin
-    pool_n = args.serve_pool
-    _, spec0 = synth.serve_trace(1000.0, pool_n)
-    pool = _gen_pool([(h, w, dt, seed) for h, w, dt, lam, seed in spec0], host_cores())
+    from paper_1603_09180_gb300 import thin
+    specs, lams = serve_pool_specs(args.serve_pool)
+    pool = _gen_pool(specs, host_cores())
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     thin.load()
-    budget = 40 << 30
-    rates = [float(r) for r in args.serve_rates.split(",")]
-
-    def drive(rate, submit, drain):
-        t_arr, spec = synth.serve_trace(rate, int(rate * args.serve_seconds) + 1, seed=int(rate))
-        sub_t, lat, rejected = {}, [], 0
-        t0 = time.perf_counter()
-        for k, ta in enumerate(t_arr):
-            now = time.perf_counter() - t0
-            if ta > now:
-                time.sleep(ta - now)
-            img = pool[k % pool_n]
-            lam = spec[k][3] * (16 if img.dtype == np.uint16 else 1)
-            ts = time.perf_counter()
-            tk = submit(img, lam)
-            if tk is None:
-                rejected += 1
-            else:
-                sub_t[tk] = ts
-        t_sub_end = time.perf_counter()
-        done_t = drain(len(sub_t))
-        for tk, td in done_t.items():
-            lat.append(td - sub_t[tk])
-        t_end = max(done_t.values()) if done_t else t_sub_end
-        # steady state: completions while requests keep arriving, after the first quarter of the window
-        w0 = t0 + 0.25 * (t_sub_end - t0)
-        in_window = sum(1 for td in done_t.values() if w0 <= td <= t_sub_end)
-        lat.sort()
-        pct = lambda q: round(1e3 * lat[min(len(lat) - 1, int(q * len(lat)))], 2) if lat else None
-        return {"rate_per_s": rate, "offered": len(t_arr), "completed": len(lat), "rejected": rejected,
-                "images_per_s": round(len(lat) / (t_end - t0), 1),
-                "steady_images_per_s": round(in_window / max(1e-9, t_sub_end - w0), 1),
-                "p50_ms": pct(0.5), "p99_ms": pct(0.99), "submit_s": round(t_sub_end - t0, 2)}
-
     out = {"served": [], "plain": []}
     with ClockSampler(0) as clk:
-        for rate in rates:
-            srv = thin.Server(budget, max_slots=args.serve_slots, queue_cap=args.serve_queue)
-            done_t, errors = {}, []
-            lock = threading.Lock()
-
-            def submit(img, lam):
-                try:
-                    return srv.submit(img, lam)
-                except thin.ThinError as e:
-                    if e.code == thin.THIN_EAGAIN:
-                        return None
-                    raise
-
-            def collector(stop):
-                while True:
-                    t = srv.wait_any(50)
-                    if t is None:
-                        if stop.is_set():
-                            return
-                        continue
-                    td = time.perf_counter()
-                    ok, res, st, rc = srv.poll(t)
-                    with lock:
-                        if ok and rc == 0:
-                            done_t[t] = td
-                        else:
-                            errors.append(rc)
-
-            stop = threading.Event()
-            col = threading.Thread(target=collector, args=(stop,), daemon=True)
-            col.start()
-
-            def drain(n):
-                t_lim = time.perf_counter() + 60
-                while time.perf_counter() < t_lim:
-                    with lock:
-                        if len(done_t) + len(errors) >= n:
-                            break
-                    time.sleep(0.002)
-                stop.set()
-                col.join()
-                return dict(done_t)
-
-            r = drive(rate, submit, drain)
-            r["errors"] = len(errors)
+        summ = serve_summary(pool, lams, dev, args.serve_slots, args.serve_queue, args.serve_seconds)
+        cap = summ["capacity_images_per_s"]
+        rates = [float(r) for r in args.serve_rates.split(",")] + [f * cap for f in (0.25, 0.5, 0.9)]
+        for rate in sorted(rates):
+            # long enough for about 2000 completions below capacity (at most 20 s)
+            secs = max(args.serve_seconds, min(20.0, 2000.0 / min(rate, cap)))
+            r = serve_served(pool, rate, secs, args.serve_slots, args.serve_queue)
             out["served"].append(r)
             print("served", json.dumps(r), file=sys.stderr, flush=True)
-            srv.close()
-
-            # plain path: one worker, one image at a time (H2D, thin_run, D2H), same queue cap
-            q = queue.Queue(maxsize=args.serve_queue)
-            done_p, errors_p = {}, []
-            nxt = [0]
-
-            def worker():
-                while True:
-                    item = q.get()
-                    if item is None:
-                        return
-                    tk, img, lam = item
-                    try:
-                        t = _to_dev(img, dev)
-                        thin.run(t, lam, stats=False)
-                        t.cpu()
-                        done_p[tk] = time.perf_counter()
-                    except Exception:
-                        errors_p.append(tk)
-
-            wt = threading.Thread(target=worker, daemon=True)
-            wt.start()
-
-            def submit_p(img, lam):
-                nxt[0] += 1
-                try:
-                    q.put_nowait((nxt[0], img, lam))
-                    return nxt[0]
-                except queue.Full:
-                    return None
-
-            def drain_p(n):
-                t_lim = time.perf_counter() + 60
-                while len(done_p) + len(errors_p) < n and time.perf_counter() < t_lim:
-                    time.sleep(0.002)
-                q.put(None)
-                wt.join(timeout=5)
-                return dict(done_p)
-
-            r = drive(rate, submit_p, drain_p)
-            r["errors"] = len(errors_p)
+        plain_cap = serve_plain(pool, 20000.0, 2.0, args.serve_queue, dev)["steady_images_per_s"]
+        for f in (0.5, 2.0):
+            r = serve_plain(pool, f * max(1.0, plain_cap), args.serve_seconds, args.serve_queue, dev)
+            r["fraction_of_plain_capacity"] = f
             out["plain"].append(r)
             print("plain", json.dumps(r), file=sys.stderr, flush=True)
-    head = out["served"][0]
-    return {"metric": "served images/s and p99 latency (Poisson arrivals)", "value": head["images_per_s"],
+    head = summ["at_half_capacity"]
+    return {"metric": "served images/s and p99 latency (Poisson arrivals)", "value": summ["capacity_images_per_s"],
             "unit": "images/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u8/u16", "data": "synthetic",
             "workload": "serve",
             "config": {"workload": "Poisson arrivals, sides log-uniform [128, 4096], u8/u16 1:1, lambda {0, 10} "
-                                   "(x16 for u16), %d-image pool cycled" % pool_n, "budget_bytes": budget,
-                       "max_slots": args.serve_slots, "queue_cap": args.serve_queue,
-                       "seconds_per_rate": args.serve_seconds},
-            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "rates": out, "clocks": clk.summary()}
+                                   "on pixel values as given, %d-image pool cycled" % args.serve_pool,
+                       "budget_bytes": SERVE_BUDGET, "max_slots": args.serve_slots, "queue_cap": args.serve_queue},
+            "p50_ms_at_half_capacity": head["p50_ms"], "p99_ms_at_half_capacity": head["p99_ms"],
+            "summary": summ, "rates": out, "plain_capacity_images_per_s": plain_cap, "clocks": clk.summary()}
 
 
 def main(argv=None):
@@ -705,10 +842,12 @@ def main(argv=None):
     ap.add_argument("--halo", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per batch (profiling runs use fewer)")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-image figures of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving figures of the default line")
     ap.add_argument("--workload", default="batch192", choices=["batch192", "large", "uneven", "serve"])
     ap.add_argument("--uneven-n", type=int, default=1024)
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-queue", type=int, default=256)

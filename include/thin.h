@@ -195,7 +195,7 @@ int thin_batch(const thin_job *jobs, int n, thin_adj adj, void *stream, const th
 typedef struct thin_plan thin_plan;
 
 /* jobs, n, adj, opt as for thin_batch (the NAIVE kernel returns
- * THIN_ERR_UNSUPPORTED).  The plan owns device memory (cudaMalloc) until it
+ * THIN_ERR_UNSUPPORTED).  The plan owns device memory (stream-ordered allocator) until it
  * is destroyed.  Synchronous: returns once the plan is ready. */
 int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_options *opt, thin_plan **out);
 
@@ -210,7 +210,8 @@ int thin_plan_stats(thin_plan *p, void *stream, thin_stats *out);
  * (all 0 when it has no tiled images or the caller fixed them). */
 int thin_plan_tiling(const thin_plan *p, int *tile_w, int *tile_h, int *halo);
 
-/* Waits for the device to be idle, then frees the plan. */
+/* Waits for the plan's last launch to finish (not for other work on the
+ * device), then frees the plan. */
 int thin_plan_destroy(thin_plan *p);
 
 /*
@@ -251,11 +252,12 @@ void thin_point_table_adj(thin_adj adj, uint32_t out[256]);
 
 /*
  * thin_run_noalloc: thin_run with the tiled engine for callers that cannot
- * allocate device memory, e.g. an application that hands every byte of device
- * memory to its own allocator up front, or code that runs while another
- * thread of the process captures a CUDA graph in global capture mode, where
- * allocation calls are refused.  The paper has no counterpart: this is a
- * property of the library, not of the method.
+ * allocate device memory when they call in: an application that hands all
+ * device memory to its own allocator at start-up (a further cudaMalloc would
+ * fail or eat into that budget), or a loop with a fixed time budget that may
+ * not call into the allocator, which can have to map new memory or wait for
+ * the device.  The paper has no counterpart: this is a property of the
+ * library, not of the method.
  *
  * Arguments, layout, result and stats are those of thin_run (the kernel
  * option is ignored: the tiled engine always runs).  Scratch memory comes
@@ -268,8 +270,9 @@ void thin_point_table_adj(thin_adj adj, uint32_t out[256]);
  *     THIN_ERR_TOO_LARGE and is left untouched.  16 MiB holds, for example,
  *     a 3500 x 3500 u8 or a 2500 x 2500 u16 image with 16-byte aligned rows
  *     (unaligned rows need the extra buffer: 2048 x 2048 u8 still fits).
- *   - The first call on a device looks up the array's device address; make it
- *     before any stream capture begins.
+ *   - The first call on a device looks up the array's device address (again
+ *     after the device's context is created anew, e.g. after cudaDeviceReset);
+ *     make that first call before any stream capture begins.
  *   - Every call uses the same array and overwrites what the previous call
  *     left there (the call itself resets everything it reads).  Calls that
  *     can overlap on the GPU -- on different streams, or from several host
@@ -287,21 +290,28 @@ const char *thin_version(void);
  * serve drive of the GPU form; the paper's own drive is the FIFO of Sec. 3.2,
  * run by CPU threads).
  *
- * A server owns four worker lanes (host threads, each with its own CUDA
- * stream) on the device that is current at thin_serve_create.  submit copies
+ * A server owns eight worker lanes (host threads, each with its own CUDA
+ * streams) on the device that is current at thin_serve_create.  submit copies
  * the host image into a pinned host buffer and returns at once with a ticket.
- * An idle lane admits queued requests in arrival order while the slot count
- * and the byte budget allow, at most max_slots / 4 of them (a request that
- * does not fit waits at the head of the queue).  It allocates their device
- * images, copies them in, thins them with one thin_batch call (large images
- * on the tiled engine, never the wide mode, so that the lanes share the GPU),
- * copies the results back and retires them, returning their bytes and slots.  Host staging is one pinned arena allocated at
- * create (a quarter of the device budget, clamped to 256 MiB .. 4 GiB), so
- * submit makes no CUDA allocation.  Requests that arrive while other batches run are
- * admitted by the next idle lane and run on the device beside them.  Each
- * image gets exactly the result thin_run gives it alone (rule MAX, default
- * options, (8,4)-adjacency).  The server's functions may be called from any
- * host threads.
+ * Requests wait in two queues: images that fit one thread-block cluster's
+ * shared memory (the resident engine), and larger ones (the tiled engine).
+ * An idle lane admits requests of one queue in arrival order while the slot
+ * count and the byte budget allow, at most max_slots / 8 of them (a request
+ * that does not fit waits at the head of its queue); one lane at a time
+ * takes from the large queue, and its tiled launch uses at most half of the
+ * SMs, so small requests keep running beside it.  The lane allocates the
+ * device images, copies them in and launches them as one batch (never the
+ * wide mode, so that the lanes share the GPU).  Each resident image is
+ * retired as soon as it is finished -- its result copied back and its bytes
+ * and slot returned -- while the rest of its batch still runs; tiled images
+ * retire when their batch ends.  Queued requests are
+ * admitted by the next idle lane as slots and memory free up, and run on the
+ * device beside the batches already there.  Host staging is one pinned arena
+ * allocated at create (a quarter of the device budget, clamped to
+ * 256 MiB .. 4 GiB), so submit makes no CUDA allocation.  Each image gets
+ * exactly the result thin_run gives it alone (rule MAX, default options,
+ * (8,4)-adjacency).  The server's functions may be called from any host
+ * threads.
  * -------------------------------------------------------------------- */
 typedef struct thin_server thin_server;
 

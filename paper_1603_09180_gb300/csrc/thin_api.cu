@@ -149,6 +149,16 @@ cudaError_t side_streams(SideStreams **out)
 
 }  // namespace
 
+cudaError_t thread_side_streams(cudaStream_t **side, cudaEvent_t **ev)
+{
+    SideStreams *ss = nullptr;
+    const cudaError_t e = side_streams(&ss);
+    if (e != cudaSuccess) return e;
+    *side = ss->s;
+    *ev = ss->ev;
+    return cudaSuccess;
+}
+
 int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, const thin_options &o,
                        cudaStream_t s, bool async_alloc)
 {
@@ -160,7 +170,8 @@ int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, 
         for (int k : grp.second) js.push_back(specs[k]);
         res.emplace_back();
         res_idx.push_back(grp.second);
-        const int rc = resident_prepare(js.data(), int(js.size()), grp.first, G.nw, o, s, async_alloc, &res.back());
+        const int rc =
+            resident_prepare(js.data(), int(js.size()), grp.first, G.nw, o, s, async_alloc, &res.back(), 0, done);
         if (rc != THIN_OK) return rc;
     }
     for (const auto &wj : G.wide) {
@@ -173,7 +184,7 @@ int Execution::prepare(const std::vector<JobSpec> &specs_in, const Grouping &G, 
         std::vector<JobSpec> js;
         for (int k : G.tiled) js.push_back(specs[k]);
         tiled_idx = G.tiled;
-        const int rc = tiled_prepare(js.data(), int(js.size()), o, s, async_alloc, &tiled);
+        const int rc = tiled_prepare(js.data(), int(js.size()), o, s, async_alloc, &tiled, tiled_max_grid);
         if (rc != THIN_OK) return rc;
     }
     return THIN_OK;
@@ -282,12 +293,6 @@ void noop_stats(const thin_options &o, thin_stats *s)
 }
 
 }  // namespace
-
-int batch_validated(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out,
-                    bool allow_wide)
-{
-    return dispatch(specs, o, s, out, allow_wide);
-}
 
 }  // namespace thin
 

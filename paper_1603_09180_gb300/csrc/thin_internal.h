@@ -30,6 +30,7 @@ struct JobSpec {
     int dtype;      // THIN_U8 / THIN_U16
     uint32_t lam;
     int adj;        // THIN_ADJ_8_4 / THIN_ADJ_4_8
+    int done_slot = -1;  // resident engine: completion record to post when the image is finished, -1 none
 };
 
 inline int elem_size(int dtype) { return dtype == THIN_U16 ? 2 : 1; }
@@ -66,7 +67,7 @@ struct ResJob {
     int hr;     // halo rows copied from each neighbouring block (even; 0 for a one-block cluster)
     int steph;  // phases between exchanges of halo rows
     int adj;    // thin_adj
-    int pad;
+    int done_slot;  // completion record of the job (ResArgs::done), -1 none
 };
 
 struct ResStat {
@@ -76,6 +77,15 @@ struct ResStat {
     long long phases;
     int converged;
     int error;
+};
+
+// Completion record of one job, in host-mapped memory: the job's stats, then
+// `flag` set to 1 (a system-scope release store) once its image is back in
+// the caller's memory.  The host resets flag to 0 before the launch.
+struct ResDone {
+    ResStat st;
+    int error;       // the launch's error word when the job finished
+    unsigned flag;
 };
 
 struct ResCtl {
@@ -101,6 +111,7 @@ struct ResArgs {
     int pad;
     unsigned char *xbuf;        // per block: 2 sides x 2 step parities x xslot bytes
     unsigned long long xslot;
+    ResDone *done;              // completion records (ResJob::done_slot), nullptr: none
 };
 
 // A resident launch prepared on the host (device tables uploaded), ready to
@@ -119,9 +130,11 @@ struct ResidentPrepared {
 // strips > 0: one image (n == 1) over `strips` clusters of C blocks, one
 // cooperative launch (the wide mode for images larger than one cluster).
 int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
-                     bool async_alloc, ResidentPrepared *R, int strips = 0);
+                     bool async_alloc, ResidentPrepared *R, int strips = 0, ResDone *done = nullptr);
 cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream);
 int resident_collect(const ResidentPrepared &R, const thin_options &opt, cudaStream_t stream, thin_stats *out);
+// The public stats of a finished resident job (error: the launch's error word).
+void resident_stats(const ResStat &S, int error, const thin_options &opt, thin_stats *o);
 void resident_release(ResidentPrepared &R, cudaStream_t stream);
 // Smallest cluster of nw-warp blocks whose shared memory holds a w x h image
 // of `dtype`, 0 if none.
@@ -135,8 +148,10 @@ int resident_wide_strips(int w, int h, int dtype, size_t smem_limit, int nw, int
 
 // A tiled launch prepared on the host (opaque; thin_tiled.cu).
 struct TiledPrepared;
+// max_grid > 0 caps the launch at that many blocks (serving keeps the rest of
+// the GPU free for the resident launches of its other lanes).
 int tiled_prepare(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, bool async_alloc,
-                  TiledPrepared **out);
+                  TiledPrepared **out, int max_grid = 0);
 cudaError_t tiled_enqueue(const TiledPrepared *T, cudaStream_t stream);
 int tiled_collect(const TiledPrepared *T, const thin_options &opt, cudaStream_t stream, thin_stats *out);
 void tiled_release(TiledPrepared *T, cudaStream_t stream);
@@ -162,10 +177,6 @@ struct Grouping {
 // the GPU.
 int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Grouping *G, bool allow_wide = true);
 
-// thin_batch on validated images (the C-ABI entry without the checks).
-int batch_validated(const std::vector<JobSpec> &specs, const thin_options &o, cudaStream_t s, thin_stats *out,
-                    bool allow_wide);
-
 // Every launch group of a batch, prepared; enqueue() is device work only
 // (resident groups forked onto up to four side streams with events, joined
 // back before the tiled group), so it can be captured in a CUDA graph.
@@ -173,6 +184,8 @@ struct Execution {
     std::vector<JobSpec> specs;
     thin_options opt;
     bool async = true;
+    ResDone *done = nullptr;  // completion records for the resident groups' jobs (JobSpec::done_slot)
+    int tiled_max_grid = 0;   // cap on the tiled launch's blocks, 0 = none
     std::vector<ResidentPrepared> res;
     std::vector<std::vector<int>> res_idx;
     std::vector<ResidentPrepared> wide;
@@ -185,6 +198,10 @@ struct Execution {
     int collect(cudaStream_t s, thin_stats *out) const;  // out[k] for specs[k]; waits for s
     void release(cudaStream_t s);
 };
+
+// Helper streams and events of the calling host thread for Execution::enqueue
+// (created once per thread and device, kept until the process exits).
+cudaError_t thread_side_streams(cudaStream_t **side, cudaEvent_t **ev);
 
 // Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.
 // Always the same value, so host threads launching the kernel at once with

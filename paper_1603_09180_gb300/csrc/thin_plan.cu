@@ -24,6 +24,9 @@ struct thin_plan {
     thin::Execution X;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;  // the plan's own stream: uploads at create, frees at destroy
+    cudaEvent_t done = nullptr;     // recorded after every launch
+    bool launched = false;
 };
 
 namespace {
@@ -31,10 +34,15 @@ namespace {
 void destroy_plan(thin_plan *p)
 {
     if (!p) return;
+    // no launch of the plan may still use its tables: wait for the last one
+    // (launches of one plan do not overlap), not for the rest of the device
+    if (p->stream && p->done && p->launched) cudaStreamWaitEvent(p->stream, p->done, 0);
+    p->X.release(p->stream);
+    if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    cudaDeviceSynchronize();  // no launch of the plan may still use its tables
-    p->X.release(nullptr);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
 
@@ -94,6 +102,8 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
     std::vector<cudaStream_t> side(4, nullptr);
     std::vector<cudaEvent_t> ev(5, nullptr);
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    p->stream = cs;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
     for (auto &x : side)
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
     for (auto &x : ev)
@@ -118,7 +128,7 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
         p->halo = ot.halo;
     }
     if (e == cudaSuccess) {
-        rc = p->X.prepare(p->specs, G, ot, cs, false);  // plan-owned device memory (cudaMalloc)
+        rc = p->X.prepare(p->specs, G, ot, cs, true);  // plan-owned device memory, stream-ordered on cs
         if (rc == THIN_OK) e = cudaStreamSynchronize(cs);  // tables uploaded before capture
         if (rc == THIN_OK && e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (rc == THIN_OK && e == cudaSuccess) {
@@ -132,7 +142,6 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
         if (x) cudaEventDestroy(x);
     for (auto x : side)
         if (x) cudaStreamDestroy(x);
-    if (cs) cudaStreamDestroy(cs);
     if (rc == THIN_OK && e != cudaSuccess) rc = cuda_status(e);
     if (rc != THIN_OK) {
         destroy_plan(p);
@@ -147,7 +156,10 @@ int thin_plan_launch(thin_plan *p, void *stream)
     NvtxRange nv("thin_plan_launch");
     if (!p) return THIN_ERR_ARG;
     if (p->idle) return THIN_OK;
-    return cuda_status(cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)));
+    cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaEventRecord(p->done, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) p->launched = true;
+    return cuda_status(e);
 }
 
 int thin_plan_stats(thin_plan *p, void *stream, thin_stats *out)

@@ -21,11 +21,14 @@
 // changed nothing anywhere in the image (its fixed point under the schedule)
 // or at the phase cap.
 //
-// Work in a phase.  Each warp scans its share of the parity's bitmap words and
-// queues the groups it finds.  With more than 32 queued groups it tests them
-// all first, packing those that lower (with their test result) to the front of
-// its queue, then lowers them on full lanes starting from that result; with
-// fewer it tests and lowers in one pass.  One block barrier ends the phase.
+// Work in a phase.  Each warp scans its share of the parity's bitmap words
+// and appends the groups it finds to one queue of the block; after a block
+// barrier the queue is split evenly over the warps, so a front that crosses
+// only part of the image still keeps every warp busy.  A warp whose share is
+// larger than 32 groups tests them all first, packing those that lower (with
+// their test result) to the front of its share, then lowers them on full
+// lanes starting from that result; with fewer it tests and lowers in one
+// pass.  One more block barrier ends the phase.
 //
 // Wide mode.  An image too large for one cluster is spread over all clusters
 // of one cooperative launch, a strip each.  Halo rows cross between clusters
@@ -80,7 +83,10 @@ struct Ctrl {
     unsigned long long ntest;
     long long peer_last[8];  // every block's `last`, pushed by the blocks themselves each phase
     int bar_ok;              // result of the last grid barrier (wide launches)
+    unsigned qn[2];          // fill counters of the block's group queue, alternating by scan round
+    unsigned fail[2];        // wide launches, cluster leader: a block's grid-barrier wait failed (by step parity)
 };
+static_assert(sizeof(Ctrl) <= kOffBar - kOffCtrl, "control words overlap the mbarrier");
 
 __host__ __device__ inline size_t res_bits_off(int rows, int rp) { return (kOffRows + size_t(rows) * rp + 15) / 16 * 16; }
 // four dirty bitmaps (one per parity), then the phase's queue of groups
@@ -168,26 +174,12 @@ __device__ bool res_grid_barrier(ResCtl *ctl, unsigned nblocks, unsigned long lo
     return *s_ok != 0;
 }
 
-// Marks, in the dirty bitmap `bm` of one parity, the group in cell row cr,
-// column cc, and the groups left (lo) and right (hi) of it.
-__device__ __forceinline__ void mark_groups(uint32_t *bm, int wpr, int cr, int cc, bool lo, bool hi)
+// OR of m into bits[key] (key < 0: nothing to mark).  Combining the lanes
+// that name the same word first (__match_any_sync + __reduce_or_sync) was
+// measured slower than letting the shared-memory atomics serialise.
+__device__ __forceinline__ void or_word(uint32_t *bits, int key, uint32_t m)
 {
-    uint32_t *row = bm + cr * wpr;
-    const int w = cc >> 5, b = cc & 31;
-    uint32_t m = 1u << b;
-    if (lo) {
-        if (b > 0)
-            m |= 1u << (b - 1);
-        else
-            atomicOr(&row[w - 1], 0x80000000u);
-    }
-    if (hi) {
-        if (b < 31)
-            m |= 1u << (b + 1);
-        else
-            atomicOr(&row[w + 1], 1u);
-    }
-    atomicOr(&row[w], m);
+    if (key >= 0) atomicOr(bits + key, m);
 }
 
 template <int NW>
@@ -246,9 +238,10 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         // dirty[q]: per parity q = 2 (y & 1) + (x & 1), one bit per 4-point group (cell row, column):
         // some neighbour of a point of the group moved since the group's last test
         uint32_t *dirty = reinterpret_cast<uint32_t *>(smem + res_bits_off(LR, RP));
+        // the block's queue of the groups found in one scan round (codes, then one test-result byte each)
         const int WQ = res_warp_queue(LR, WPR, NW);
-        uint16_t *wqueue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR)) + warp * WQ;
-        uint8_t *wok = smem + res_queue_off(LR, RP, WPR) + size_t(2) * NW * WQ + size_t(warp) * WQ;
+        uint16_t *bqueue = reinterpret_cast<uint16_t *>(smem + res_queue_off(LR, RP, WPR));
+        uint8_t *bok = smem + res_queue_off(LR, RP, WPR) + size_t(2) * NW * WQ;
         const int row0 = gb * R;         // first own image row
         const int ybase = row0 - HR;     // image row of shared row 0
         const int rowb = J.w * es;
@@ -288,6 +281,10 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             ctrl->last = -1;
             ctrl->nlow = 0;
             ctrl->ntest = 0;
+            ctrl->qn[0] = 0u;
+            ctrl->qn[1] = 0u;
+            ctrl->fail[0] = 0u;
+            ctrl->fail[1] = 0u;
         }
         if (tid < 8) ctrl->peer_last[tid] = -1;
         __syncthreads();
@@ -297,6 +294,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         const uint32_t *comp = tabs + 256;
 
         long long g = P.start_phase;
+        unsigned qround = 0;  // scan rounds so far: selects the queue counter
         long long steps = 0;
         int converged = 0;
         int nlow = 0, ntest = 0;
@@ -307,25 +305,31 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             for (int j = 0; j < Hs; ++j, ++g) {
                 const int p = int(g & 3), px = p & 1, py = p >> 1;
                 uint32_t *dp = dirty + p * slot_words;
-                uint32_t *d_row = dirty + (2 * py + (px ^ 1)) * slot_words;   // same rows, other columns
-                uint32_t *d_col = dirty + (2 * (py ^ 1) + px) * slot_words;   // rows above and below
-                uint32_t *d_diag = dirty + (2 * (py ^ 1) + (px ^ 1)) * slot_words;
                 // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
                 const int rr = B > 1 ? Hs - 1 - j : 0;
                 const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
                 // the groups of the other three parities next to a moved point become dirty
+                // (moved == 0: nothing to mark)
+                const int qrow = 2 * py + (px ^ 1), qcol = 2 * (py ^ 1) + px, qdiag = 2 * (py ^ 1) + (px ^ 1);
                 auto mark = [&](int cr, int cc, uint32_t moved) {
                     const bool lo = px == 0 && (moved & 1u);           // x - 1 of point 0 is left of the block
                     const bool hi = px == 1 && (moved & 0x01000000u);  // x + 1 of point 3 is right of it
-                    mark_groups(d_row, WPR, cr, cc, lo, hi);
+                    const int w = cc >> 5, b = cc & 31;
+                    const uint32_t mc = 1u << b;
+                    const uint32_t mlr = mc | (lo && b > 0 ? mc >> 1 : 0u) | (hi && b < 31 ? mc << 1 : 0u);
                     const int ca = cr - 1 + py, cb = cr + py;          // cell rows of rows y - 1, y + 1
-                    if (ca >= 0) {
-                        mark_groups(d_col, WPR, ca, cc, false, false);
-                        mark_groups(d_diag, WPR, ca, cc, lo, hi);
-                    }
-                    if (cb < CRT) {
-                        mark_groups(d_col, WPR, cb, cc, false, false);
-                        mark_groups(d_diag, WPR, cb, cc, lo, hi);
+                    const bool mv = moved != 0, va = mv && ca >= 0, vb = mv && cb < CRT;
+                    or_word(dirty, mv ? qrow * slot_words + cr * WPR + w : -1, mlr);
+                    or_word(dirty, va ? qcol * slot_words + ca * WPR + w : -1, mc);
+                    or_word(dirty, va ? qdiag * slot_words + ca * WPR + w : -1, mlr);
+                    or_word(dirty, vb ? qcol * slot_words + cb * WPR + w : -1, mc);
+                    or_word(dirty, vb ? qdiag * slot_words + cb * WPR + w : -1, mlr);
+                    if ((lo && b == 0) || (hi && b == 31)) {  // the group across a word boundary (rare)
+                        const int ws = lo && b == 0 ? w - 1 : w + 1;
+                        const uint32_t ms = lo && b == 0 ? 0x80000000u : 1u;
+                        atomicOr(&dirty[qrow * slot_words + cr * WPR + ws], ms);
+                        if (va) atomicOr(&dirty[qdiag * slot_words + ca * WPR + ws], ms);
+                        if (vb) atomicOr(&dirty[qdiag * slot_words + cb * WPR + ws], ms);
                     }
                 };
                 auto where = [&](int code, int &cr, int &cc, uint32_t &vm, uint32_t &in) {
@@ -341,115 +345,129 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                     in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
                 };
                 bool moved_own = false;
-                // Each warp takes the bitmap words warp, warp + NW, ... of this parity,
-                // consumes their bits, and tests and lowers the groups it found on its
-                // own: no block barrier until the end of the phase.
+                // A scan round: each warp takes the bitmap words warp, warp + NW, ... of this parity
+                // (one per lane), consumes their bits and appends the groups it found to the block's
+                // queue.  After a block barrier the queue is split evenly over the warps, and each
+                // warp tests and lowers its share on its own: no other block barrier until the end
+                // of the phase (or of the round, when the bitmap needs several).
                 for (int r0 = 0; r0 < slot_words; r0 += 32 * NW) {
-                    const int wi = r0 + lane * NW + warp;
-                    uint32_t d = 0;
-                    int cr = 0;
-                    if (wi < slot_words) {
-                        cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
-                        const int i = wi - cr * WPR;
-                        const int y = ybase + 2 * cr + py;
-                        if (y >= ylo && y <= yhi) {
-                            const int valid = CW - 32 * i;
-                            d = dp[wi] & (valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u));
-                        }
-                        if (dp[wi]) dp[wi] = 0u;
-                    }
-                    const int cnt = __popc(d);
-                    int incl = cnt;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const int nq = __shfl_sync(0xffffffffu, incl, 31);
-                    if (nq == 0) continue;
                     {
-                        int pos = incl - cnt;
-                        const int cbase = (wi - cr * WPR) * 32 + cr * CW;
-                        while (d) {
-                            const int b = __ffs(d) - 1;
-                            d &= d - 1;
-                            wqueue[pos++] = uint16_t(cbase + b);
+                        const int wi = r0 + lane * NW + warp;
+                        uint32_t d = 0;
+                        int cr = 0;
+                        if (wi < slot_words) {
+                            cr = WPR > 1 ? int(__umulhi(uint32_t(wi), Mwpr)) : wi;
+                            const int i = wi - cr * WPR;
+                            const int y = ybase + 2 * cr + py;
+                            if (y >= ylo && y <= yhi) {
+                                const int valid = CW - 32 * i;
+                                d = dp[wi] & (valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u));
+                            }
+                            if (dp[wi]) dp[wi] = 0u;
+                        }
+                        const int cnt = __popc(d);
+                        int incl = cnt;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += v;
+                        }
+                        const int wsum = __shfl_sync(0xffffffffu, incl, 31);
+                        if (wsum) {
+                            int base = 0;
+                            if (lane == 31) base = int(atomicAdd(&ctrl->qn[qround & 1], unsigned(wsum)));
+                            int pos = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+                            const int cbase = (wi - cr * WPR) * 32 + cr * CW;
+                            while (d) {
+                                const int bb = __ffs(d) - 1;
+                                d &= d - 1;
+                                bqueue[pos++] = uint16_t(cbase + bb);
+                            }
                         }
                     }
-                    __syncwarp();
-                    int nl = nq;
-                    if (!simd || nq > kTwoPass) {
-                        // test first; the groups that lower are packed to the front of the queue
-                        // (in place: a chunk's slots are read before any of them is written)
-                        nl = 0;
-                        for (int kb = 0; kb < nq; kb += 32) {
-                            const int k = kb + lane;
-                            bool lowers = false;
-                            int code = 0;
-                            if (k < nq) {
-                                code = wqueue[k];
-                                int gcr, gcc;
-                                uint32_t vm, in;
-                                where(code, gcr, gcc, vm, in);
-                                ntest += __popc(in);
-                                uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
-                                if (simd) {
-                                    const uint32_t okb = (kFix && mode == 0)
-                                                             ? test_u8<0>(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode)
-                                                             : test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode);
-                                    lowers = okb != 0;
-                                    code |= int((okb | (okb >> 7) | (okb >> 14) | (okb >> 21)) & 0xfu) << 16;
-                                } else {
-                                    const uint32_t moved =
-                                        es == 2 ? item_table<uint16_t>(reinterpret_cast<const uint16_t *>(rb - RP),
-                                                                       reinterpret_cast<uint16_t *>(rb),
-                                                                       reinterpret_cast<const uint16_t *>(rb + RP), px, vm,
-                                                                       in, ptab, J.lam, mode, nlow)
-                                                : item_table<uint8_t>(rb - RP, rb, rb + RP, px, vm, in, ptab, J.lam, mode,
-                                                                      nlow);
-                                    if (moved) {
-                                        mark(gcr, gcc, moved);
-                                        if (moved & in) moved_own = true;
+                    __syncthreads();
+                    const int N = int(*reinterpret_cast<volatile unsigned *>(&ctrl->qn[qround & 1]));
+                    if (tid == 0) ctrl->qn[(qround + 1) & 1] = 0u;  // last read in the previous round
+                    ++qround;
+                    const int qa = (N * warp) / NW;
+                    const int nq = (N * (warp + 1)) / NW - qa;  // this warp's share: queue slots qa .. qa + nq - 1
+                    uint16_t *wqueue = bqueue + qa;
+                    uint8_t *wok = bok + qa;
+                    if (nq > 0) {
+                        int nl = nq;
+                        if (!simd || nq > kTwoPass) {
+                            // test first; the groups that lower are packed to the front of the share
+                            // (in place: a chunk's slots are read before any of them is written)
+                            nl = 0;
+                            for (int kb = 0; kb < nq; kb += 32) {
+                                const int k = kb + lane;
+                                bool lowers = false;
+                                int code = 0, gcr = 0, gcc = 0;
+                                uint32_t tmoved = 0;
+                                if (k < nq) {
+                                    code = wqueue[k];
+                                    uint32_t vm, in;
+                                    where(code, gcr, gcc, vm, in);
+                                    ntest += __popc(in);
+                                    uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
+                                    if (simd) {
+                                        const uint32_t okb =
+                                            (kFix && mode == 0) ? test_u8<0>(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode)
+                                                                : test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode);
+                                        lowers = okb != 0;
+                                        code |= int((okb | (okb >> 7) | (okb >> 14) | (okb >> 21)) & 0xfu) << 16;
+                                    } else {
+                                        tmoved = es == 2 ? item_table<uint16_t>(
+                                                               reinterpret_cast<const uint16_t *>(rb - RP),
+                                                               reinterpret_cast<uint16_t *>(rb),
+                                                               reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in,
+                                                               ptab, J.lam, mode, nlow)
+                                                         : item_table<uint8_t>(rb - RP, rb, rb + RP, px, vm, in, ptab,
+                                                                               J.lam, mode, nlow);
+                                        if (tmoved & in) moved_own = true;
                                     }
                                 }
+                                if (!simd) mark(gcr, gcc, tmoved);
+                                const unsigned bal = __ballot_sync(0xffffffffu, lowers);
+                                if (lowers) {
+                                    const int at = nl + __popc(bal & ((1u << lane) - 1u));
+                                    wqueue[at] = uint16_t(code);
+                                    wok[at] = uint8_t(code >> 16);  // which of the four points passed the test
+                                }
+                                nl += __popc(bal);
                             }
-                            const unsigned bal = __ballot_sync(0xffffffffu, lowers);
-                            if (lowers) {
-                                const int at = nl + __popc(bal & ((1u << lane) - 1u));
-                                wqueue[at] = uint16_t(code);
-                                wok[at] = uint8_t(code >> 16);  // which of the four points passed the test
+                            __syncwarp();
+                            if (!simd) nl = 0;
+                        }
+                        // lower them (u8, (8,4)); with few groups the loop's first test is the only one
+                        for (int kb = 0; kb < nl; kb += 32) {
+                            const int k = kb + lane;
+                            int gcr = 0, gcc = 0;
+                            uint32_t moved = 0;
+                            if (k < nl) {
+                                const int code = wqueue[k];
+                                uint32_t vm, in;
+                                where(code, gcr, gcc, vm, in);
+                                if (nq <= kTwoPass) ntest += __popc(in);
+                                uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
+                                if (kOkPass && nq > kTwoPass) {  // tested in the first pass: start lowering at once
+                                    const uint32_t o4 = wok[k];
+                                    const uint32_t okb = (o4 & 1u) | ((o4 & 2u) << 7) | ((o4 & 4u) << 14) | ((o4 & 8u) << 21);
+                                    moved = (kFix && mode == 0)
+                                                ? item_u8_tested<0>(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow)
+                                                : item_u8_tested(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow);
+                                } else {
+                                    moved = (kFix && mode == 0)
+                                                ? item_u8<0>(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow)
+                                                : item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
+                                }
+                                if (moved & in) moved_own = true;
                             }
-                            nl += __popc(bal);
+                            mark(gcr, gcc, moved);
                         }
                         __syncwarp();
-                        if (!simd) nl = 0;
                     }
-                    // lower them (u8, (8,4)); with few groups the loop's first test is the only one
-                    for (int k = lane; k < nl; k += 32) {
-                        const int code = wqueue[k];
-                        int gcr, gcc;
-                        uint32_t vm, in;
-                        where(code, gcr, gcc, vm, in);
-                        if (nq <= kTwoPass) ntest += __popc(in);
-                        uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
-                        uint32_t moved;
-                        if (kOkPass && nq > kTwoPass) {  // tested in the first pass: start lowering at once
-                            const uint32_t o4 = wok[k];
-                            const uint32_t okb = (o4 & 1u) | ((o4 & 2u) << 7) | ((o4 & 4u) << 14) | ((o4 & 8u) << 21);
-                            moved = (kFix && mode == 0)
-                                        ? item_u8_tested<0>(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow)
-                                        : item_u8_tested(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow);
-                        } else {
-                            moved = (kFix && mode == 0)
-                                        ? item_u8<0>(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow)
-                                        : item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
-                        }
-                        if (moved) {
-                            mark(gcr, gcc, moved);
-                            if (moved & in) moved_own = true;
-                        }
-                    }
-                    __syncwarp();
+                    if (r0 + 32 * NW < slot_words) __syncthreads();  // the next round refills the queue
                 }
                 if (__syncthreads_or(moved_own) && tid == 0) ctrl->last = g;
             }
@@ -478,7 +496,15 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                 if (rank == C - 1 && strip + 1 < S) publish(1, R, R / 2);        // my last own rows, for the strip below
                 if (tid == 0) atomicMax(&P.ctl->gl_last, ctrl->last);
                 __threadfence();
-                if (!res_grid_barrier(P.ctl, gridDim.x, P.timeout_ns, &ctrl->bar_ok)) break;
+                const bool bar_ok = res_grid_barrier(P.ctl, gridDim.x, P.timeout_ns, &ctrl->bar_ok);
+                // The blocks of a cluster leave the step loop together or not at all, so that their
+                // cluster barriers keep pairing up: a block whose wait failed posts it to the leader.
+                Ctrl *lead = cluster.map_shared_rank(ctrl, 0);
+                if (tid == 0 && !bar_ok) atomicOr(&lead->fail[sp], 1u);
+                cluster.sync();
+                const bool cluster_ok = *reinterpret_cast<volatile unsigned *>(&lead->fail[sp]) == 0u;
+                if (rank == 0 && tid == 0) ctrl->fail[sp ^ 1] = 0u;  // read by the cluster one step ago
+                if (!cluster_ok) break;
                 lc = *reinterpret_cast<volatile long long *>(&P.ctl->gl_last);
             } else {
                 if (tid < C) cluster.map_shared_rank(ctrl, tid)->peer_last[rank] = ctrl->last;  // push to every block
@@ -585,7 +611,24 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the next bulk copy
+        const bool post = P.done != nullptr && J.done_slot >= 0;
+        if (post) __threadfence_system();  // this block's rows are out before the leader posts the record
         cluster.sync();  // nobody reads this job's rows or control words any more
+        if (post && rank == 0 && tid == 0) {
+            // completion record: the job's stats (every block added its counts before the cluster barrier),
+            // then the flag, released at system scope for the host that polls it
+            const volatile ResStat &S = P.st[job];
+            ResDone *d = P.done + J.done_slot;
+            d->st.lowered = S.lowered;
+            d->st.tested = S.tested;
+            d->st.last_change = S.last_change;
+            d->st.phases = S.phases;
+            d->st.converged = S.converged;
+            d->st.error = 0;
+            d->error = *reinterpret_cast<volatile int *>(&P.ctl->error);
+            __threadfence_system();
+            asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(&d->flag), "r"(1u) : "memory");
+        }
     }
 }
 
@@ -719,7 +762,7 @@ size_t resident_smem_limit(int blocks)
 // Host-side preparation of one launch: job table (longest first), stats and
 // control words, and their pristine copies, all in one device allocation.
 int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
-                     bool async_alloc, ResidentPrepared *R, int strips)
+                     bool async_alloc, ResidentPrepared *R, int strips, ResDone *done)
 {
     *R = ResidentPrepared();
     R->n = n;
@@ -756,6 +799,7 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
         r.bulk = (reinterpret_cast<uintptr_t>(J.img) % 16 == 0) && (J.pitch % 16 == 0) && ((size_t(J.w) * es) % 16 == 0);
         r.index = k;
         r.adj = J.adj;
+        r.done_slot = strips > 0 ? -1 : J.done_slot;
         const int held = r.rows + 2 * r.hr;
         const size_t need = res_smem_bytes(held, r.rp, r.wpr, nw);
         if (need > limit || held / 2 * r.cw > 65535) return THIN_ERR_ARG;
@@ -822,6 +866,7 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     P.strips = strips;
     P.xbuf = strips > 0 ? reinterpret_cast<unsigned char *>(R->base + o_x) : nullptr;
     P.xslot = xslot;
+    P.done = strips > 0 ? nullptr : done;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
     if (e == cudaSuccess) {
         const int want = strips > 0 ? strips : n;  // clusters wanted
@@ -861,21 +906,25 @@ int resident_collect(const ResidentPrepared &R, const thin_options &opt, cudaStr
     if (e != cudaSuccess) return cuda_status(e);
     int rc = THIN_OK;
     for (int k = 0; k < n; ++k) {
-        const ResStat &S = st[k];
         thin_stats &o = out[R.order[k]];
-        std::memset(&o, 0, sizeof o);
-        o.converged = S.converged && !ctl.error;
-        o.status = ctl.error ? ctl.error : (o.converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
-        o.phases = S.phases;
-        o.lowered = (int64_t)S.lowered;
-        o.last_change_phase = S.last_change;
-        o.end_phase = opt.start_phase + S.phases;
-        o.tiles_visited = 0;
-        o.steps = S.phases;
-        o.tested = (int64_t)S.tested;
+        resident_stats(st[k], ctl.error, opt, &o);
         if (o.status != THIN_OK && rc == THIN_OK) rc = o.status;
     }
     return rc;
+}
+
+void resident_stats(const ResStat &S, int error, const thin_options &opt, thin_stats *o)
+{
+    std::memset(o, 0, sizeof *o);
+    o->converged = S.converged && !error;
+    o->status = error ? error : (o->converged ? THIN_OK : THIN_ERR_NOT_CONVERGED);
+    o->phases = S.phases;
+    o->lowered = (int64_t)S.lowered;
+    o->last_change_phase = S.last_change;
+    o->end_phase = opt.start_phase + S.phases;
+    o->tiles_visited = 0;
+    o->steps = S.phases;
+    o->tested = (int64_t)S.tested;
 }
 
 void resident_release(ResidentPrepared &R, cudaStream_t stream)

@@ -1,16 +1,22 @@
 // thin_serve.cu -- serving: continuous batching under a device-memory budget.
 //
-// A server owns a few worker lanes, each a host thread with its own CUDA
-// stream.  submit copies the caller's image into a pinned host buffer and
+// A server owns eight worker lanes, each a host thread with its own CUDA
+// streams.  submit copies the caller's image into a pinned host buffer and
 // queues it.  An idle lane admits queued requests in arrival order while the
-// slot count and the byte budget allow, allocates their device images, copies
-// them in, thins them all with one thin_batch call, copies the results back
-// and retires them, returning their bytes and slots at once.  Requests that
-// arrive while a lane is busy are admitted by the next idle lane, so their
-// work runs on the device next to the batches already there (the resident
-// engine gives each image its own thread-block cluster and takes only the
-// SMs it needs).  Each image's result depends only on the image and its
-// lambda: it is the same alone and in any mix.
+// slot count and the byte budget allow (at most its share of the slots),
+// allocates their device images, copies them in and launches them as one
+// batch.  Images that fit a thread-block cluster run on the resident engine,
+// which posts a completion record for each image as soon as that image is
+// finished; the lane then copies the image back on a second stream and
+// retires the request at once, returning its bytes and slot while the rest
+// of the batch still runs, so queued requests are admitted by the next idle
+// lane as slots and memory free up.  Images too large for a cluster wait in
+// a queue of their own; one lane at a time runs a batch of them on the tiled
+// engine, on at most half of the SMs, and they retire when that batch ends.
+// So small requests keep flowing on the other SMs while a large one runs.
+// Lanes run side by side on the device (the resident engine gives each image
+// its own cluster and takes only the SMs it needs).  Each image's result depends
+// only on the image and its lambda: it is the same alone and in any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +35,7 @@
 namespace thin {
 namespace {
 
-constexpr int kLanes = 4;          // batches in flight at once
+constexpr int kLanes = 8;          // batches in flight at once
 constexpr int kMaxBatch = 512;     // requests one lane admits at a time
 
 enum ReqState { kQueued, kRunning, kDone };
@@ -46,6 +52,7 @@ struct Req {
     void *dev;
     int state;
     int rc;
+    bool large;       // too large for one cluster's shared memory: the tiled engine
     thin_stats st;
 };
 
@@ -120,7 +127,10 @@ struct thin_server {
     int device = 0;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<thin::Req *> queue;
+    std::deque<thin::Req *> queue;        // requests that fit a cluster (the resident engine)
+    std::deque<thin::Req *> queue_large;  // the rest (the tiled engine)
+    bool large_busy = false;              // a lane is running a batch of large requests
+    size_t res_smem_limit = 0;            // a resident block's shared memory (one block per SM)
     std::unordered_map<uint64_t, thin::Req *> reqs;
     std::deque<uint64_t> finished;  // tickets in the order they finished, for thin_serve_wait_any
     size_t used = 0;   // bytes charged by admitted requests
@@ -145,94 +155,207 @@ size_t charge_of(int w, int h, int dtype, size_t *dpitch)
     return img + img + size_t(w) * h / 4 + (64 << 10);
 }
 
+// Ends a request: its result is in r->host (or r->rc holds its error);
+// returns its bytes and slot and posts it to the completion queue.  A client
+// may poll and free the request as soon as this returns: the caller must not
+// touch r afterwards.
+void retire(thin_server *S, Req *r)
+{
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        r->dev = nullptr;
+        r->state = kDone;
+        S->used -= r->charge;
+        --S->in_flight;
+        S->finished.push_back(r->ticket);
+        // callers that only poll never drain the list: keep it bounded
+        const size_t cap = 4 * size_t(S->max_slots + S->queue_cap);
+        while (S->finished.size() > cap) S->finished.pop_front();
+    }
+    S->cv.notify_all();
+}
+
 void lane_main(thin_server *S)
 {
     cudaSetDevice(S->device);
-    cudaStream_t stream = nullptr;
-    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t stream = nullptr, copy = nullptr;
+    ResDone *done_host = nullptr, *done_dev = nullptr;
+    std::vector<cudaEvent_t> copied(kMaxBatch, nullptr);
+    bool ok_lane = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaHostAlloc(reinterpret_cast<void **>(&done_host), sizeof(ResDone) * kMaxBatch,
+                                 cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
+                   cudaHostGetDevicePointer(reinterpret_cast<void **>(&done_dev), done_host, 0) == cudaSuccess;
+    for (auto &e : copied)
+        if (ok_lane) ok_lane = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok_lane) cudaGetLastError();
+    cudaStream_t *side = nullptr;
+    cudaEvent_t *side_ev = nullptr;
+    if (ok_lane && thread_side_streams(&side, &side_ev) != cudaSuccess) {
         cudaGetLastError();
-        stream = nullptr;
+        ok_lane = false;
     }
+    // a large batch's tiled launch takes at most half of the SMs, so that the resident
+    // launches of the other lanes keep running beside it
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+    const int tiled_cap = std::max(1, sms / 2);
     std::vector<Req *> batch;
-    std::vector<thin_stats> st;
     for (;;) {
         batch.clear();
+        bool large = false;
         {
             std::unique_lock<std::mutex> g(S->mu);
-            // wait for work that fits, or for the stop signal
+            // wait for work that fits, or for the stop signal; large requests run one batch at a time
+            auto fits = [&](const std::deque<Req *> &q) {
+                return !q.empty() && S->used + q.front()->charge <= S->budget;
+            };
             S->cv.wait(g, [&] {
                 if (S->stop) return true;
-                if (S->queue.empty() || S->in_flight >= S->max_slots) return false;
-                return S->used + S->queue.front()->charge <= S->budget;
+                if (S->in_flight >= S->max_slots) return false;
+                return fits(S->queue) || (!S->large_busy && fits(S->queue_large));
             });
             if (S->stop) break;
+            large = !S->large_busy && fits(S->queue_large);
+            if (large) S->large_busy = true;
+            std::deque<Req *> &q = large ? S->queue_large : S->queue;
             // a lane takes at most its share of the slots, so that under load the other lanes
-            // keep admitting while one lane's batch waits for its slowest image
+            // keep admitting while this lane's batch runs
             const int share = std::max(1, std::min(kMaxBatch, S->max_slots / kLanes));
-            while (!S->queue.empty() && S->in_flight < S->max_slots && int(batch.size()) < share) {
-                Req *r = S->queue.front();
+            while (!q.empty() && S->in_flight < S->max_slots && int(batch.size()) < share) {
+                Req *r = q.front();
                 if (S->used + r->charge > S->budget) break;
-                S->queue.pop_front();
+                q.pop_front();
                 S->used += r->charge;
                 ++S->in_flight;
                 r->state = kRunning;
                 batch.push_back(r);
             }
+            if (batch.empty() && large) S->large_busy = false;
         }
         if (batch.empty()) continue;
         NvtxRange nv("thin_serve batch");
-        // device slots, input copies, one batch, result copies
+        // device images and input copies
         std::vector<JobSpec> jobs;
-        std::vector<Req *> ok;
-        for (Req *r : batch) {
+        std::vector<Req *> run;
+        std::vector<char> in_run(batch.size(), 0);
+        for (size_t i = 0; i < batch.size(); ++i) {
+            Req *r = batch[i];
             r->rc = THIN_OK;
             r->dev = nullptr;
-            cudaError_t e = stream ? cudaMallocAsync(&r->dev, r->dpitch * r->h, stream) : cudaErrorInvalidResourceHandle;
+            cudaError_t e = ok_lane ? cudaMallocAsync(&r->dev, r->dpitch * r->h, stream) : cudaErrorInvalidResourceHandle;
             if (e == cudaSuccess)
                 e = cudaMemcpy2DAsync(r->dev, r->dpitch, r->host, r->row, r->row, r->h, cudaMemcpyHostToDevice, stream);
             if (e != cudaSuccess) {
+                cudaGetLastError();
                 r->rc = cuda_status(e);
                 continue;
             }
-            jobs.push_back(JobSpec{r->dev, r->w, r->h, r->dpitch, r->dtype, r->lam, THIN_ADJ_8_4});
-            ok.push_back(r);
+            JobSpec j{r->dev, r->w, r->h, r->dpitch, r->dtype, r->lam, THIN_ADJ_8_4};
+            j.done_slot = int(run.size());
+            jobs.push_back(j);
+            run.push_back(r);
+            in_run[i] = 1;
         }
-        st.assign(ok.size(), thin_stats{});
+        const int n = int(run.size());
+        // 0: running, 1: result copy in flight, 2: retired
+        std::vector<int> phase(n, 0);
+        int retired = 0;
         int rc = THIN_OK;
-        if (!ok.empty()) {
+        thin_options o;
+        thin_default_options(&o);
+        Grouping G;
+        Execution X;
+        X.done = done_dev;
+        X.tiled_max_grid = tiled_cap;
+        bool launched = false;
+        if (n > 0) {
+            for (int k = 0; k < n; ++k) done_host[k].flag = 0u;
             // the lanes share the GPU: no wide launch (it would hold every SM for one image)
-            thin_options o;
-            thin_default_options(&o);
-            rc = batch_validated(jobs, o, stream, st.data(), false);
-        }
-        for (size_t k = 0; k < ok.size(); ++k) {
-            Req *r = ok[k];
-            r->st = st[k];
-            if (r->st.status != THIN_OK) r->rc = r->st.status;
-            else if (rc != THIN_OK && rc != THIN_ERR_NOT_CONVERGED) r->rc = rc;
-            const cudaError_t e =
-                cudaMemcpy2DAsync(r->host, r->row, r->dev, r->dpitch, r->row, r->h, cudaMemcpyDeviceToHost, stream);
-            if (e != cudaSuccess && r->rc == THIN_OK) r->rc = cuda_status(e);
-        }
-        for (Req *r : batch)
-            if (r->dev) cudaFreeAsync(r->dev, stream);
-        const cudaError_t e = stream ? cudaStreamSynchronize(stream) : cudaSuccess;
-        {
-            std::lock_guard<std::mutex> g(S->mu);
-            for (Req *r : batch) {
-                if (e != cudaSuccess && r->rc == THIN_OK) r->rc = cuda_status(e);
-                r->dev = nullptr;
-                r->state = kDone;
-                S->used -= r->charge;
-                --S->in_flight;
-                S->finished.push_back(r->ticket);
+            rc = group_jobs(jobs, o, &G, false);
+            if (rc == THIN_OK) rc = X.prepare(jobs, G, o, stream, true);
+            if (rc == THIN_OK) {
+                const cudaError_t e = X.enqueue(stream, side, side_ev);
+                if (e != cudaSuccess) rc = cuda_status(e);
+                else launched = true;
             }
-            // callers that only poll never drain the list: keep it bounded
-            const size_t cap = 4 * size_t(S->max_slots + S->queue_cap);
-            while (S->finished.size() > cap) S->finished.pop_front();
         }
-        S->cv.notify_all();
+        // retire each resident image as its completion record appears; the rest when the stream is done
+        auto start_copy = [&](int k) {
+            Req *r = run[k];
+            const cudaError_t e =
+                cudaMemcpy2DAsync(r->host, r->row, r->dev, r->dpitch, r->row, r->h, cudaMemcpyDeviceToHost, copy);
+            if (e == cudaSuccess) cudaEventRecord(copied[k], copy);
+            else if (r->rc == THIN_OK) r->rc = cuda_status(e);
+            phase[k] = 1;
+        };
+        auto finish_copy = [&](int k, bool wait) {
+            if (wait) cudaEventSynchronize(copied[k]);
+            else if (cudaEventQuery(copied[k]) != cudaSuccess) return false;
+            Req *r = run[k];
+            cudaFreeAsync(r->dev, copy);
+            phase[k] = 2;
+            ++retired;
+            retire(S, r);
+            return true;
+        };
+        while (launched && retired < n) {
+            bool progress = false;
+            for (int k = 0; k < n; ++k) {
+                if (phase[k] == 0 && __atomic_load_n(&done_host[k].flag, __ATOMIC_ACQUIRE) == 1u) {
+                    resident_stats(done_host[k].st, done_host[k].error, o, &run[k]->st);
+                    if (run[k]->st.status != THIN_OK) run[k]->rc = run[k]->st.status;
+                    start_copy(k);
+                    progress = true;
+                }
+                if (phase[k] == 1) progress |= finish_copy(k, false);
+            }
+            if (progress) continue;
+            if (cudaStreamQuery(stream) != cudaErrorNotReady) break;  // the batch is over (or failed)
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        // what is left: tiled images, and any image the batch ended without posting
+        if (n > 0) {
+            std::vector<thin_stats> st(n);
+            if (launched) {
+                const int crc = X.collect(stream, st.data());  // waits for the stream
+                if (rc == THIN_OK && crc != THIN_OK && crc != THIN_ERR_NOT_CONVERGED) rc = crc;
+            } else if (stream) {
+                cudaStreamSynchronize(stream);  // the input copies are done before the copy stream reads back
+            }
+            for (int k = 0; k < n; ++k) {
+                if (phase[k] != 0) continue;
+                Req *r = run[k];
+                r->st = st[k];
+                if (r->st.status != THIN_OK) r->rc = r->st.status;
+                else if (rc != THIN_OK) r->rc = rc;
+                start_copy(k);
+            }
+            for (int k = 0; k < n; ++k)
+                if (phase[k] == 1) finish_copy(k, true);
+        }
+        X.release(stream);
+        const cudaError_t e = stream ? cudaStreamSynchronize(stream) : cudaSuccess;
+        if (e != cudaSuccess) cudaGetLastError();
+        for (size_t i = 0; i < batch.size(); ++i) {  // requests whose device image could not be set up
+            if (in_run[i]) continue;  // retired above (and perhaps already freed by a poll)
+            Req *r = batch[i];
+            if (r->dev) cudaFreeAsync(r->dev, stream);
+            retire(S, r);
+        }
+        if (large) {
+            {
+                std::lock_guard<std::mutex> g(S->mu);
+                S->large_busy = false;
+            }
+            S->cv.notify_all();
+        }
     }
+    if (copy) cudaStreamSynchronize(copy);
+    for (auto e : copied)
+        if (e) cudaEventDestroy(e);
+    if (done_host) cudaFreeHost(done_host);
+    if (copy) cudaStreamDestroy(copy);
     if (stream) cudaStreamDestroy(stream);
 }
 
@@ -257,6 +380,7 @@ int thin_serve_create(size_t device_budget_bytes, int max_slots, int queue_cap, 
         delete S;
         return THIN_ERR_CUDA;
     }
+    S->res_smem_limit = resident_smem_limit(1);
     // host staging for waiting and running requests: a quarter of the device
     // budget, between 256 MiB and 4 GiB
     const size_t host = std::min<size_t>(std::max<size_t>(device_budget_bytes / 4, size_t(256) << 20), size_t(4) << 30);
@@ -294,11 +418,12 @@ int thin_serve_submit(thin_server *S, const void *host_img, int w, int h, size_t
             delete r;
             return THIN_ERR_ARG;
         }
-        if (int(S->queue.size()) >= S->queue_cap) {
+        if (int(S->queue.size() + S->queue_large.size()) >= S->queue_cap) {
             delete r;
             return THIN_EAGAIN;
         }
     }
+    r->large = resident_cluster_size(w, h, dt, S->res_smem_limit, 16, nullptr, nullptr) == 0;
     if (row * h > S->pool.size()) {
         delete r;
         return THIN_ERR_TOO_LARGE;  // could never be staged
@@ -313,7 +438,7 @@ int thin_serve_submit(thin_server *S, const void *host_img, int w, int h, size_t
                     row);
     {
         std::lock_guard<std::mutex> g(S->mu);
-        if (int(S->queue.size()) >= S->queue_cap) {
+        if (int(S->queue.size() + S->queue_large.size()) >= S->queue_cap) {
             S->pool.put(r->host, r->host_cap);
             delete r;
             return THIN_EAGAIN;
@@ -327,7 +452,7 @@ int thin_serve_submit(thin_server *S, const void *host_img, int w, int h, size_t
             S->finished.push_back(r->ticket);
         } else {
             r->state = kQueued;
-            S->queue.push_back(r);
+            (r->large ? S->queue_large : S->queue).push_back(r);
         }
         S->reqs[r->ticket] = r;
     }

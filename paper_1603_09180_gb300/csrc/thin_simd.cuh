@@ -88,6 +88,24 @@ __device__ __forceinline__ uint32_t alpha4(const uint32_t nb[8], uint32_t M)
 #undef THIN_LOWER_NB
 }
 
+// Bit 7 set in each byte where a and b are equal.
+__device__ __forceinline__ uint32_t eq8(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;
+    return ~(((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & kMsb8;
+}
+
+// Masks of the neighbours equal to the centre values c (byte k = mask of point k).
+// A point just lowered to c = alpha^- loses exactly these from its lower mask:
+// every other lower neighbour is below alpha^-, every other neighbour above c.
+__device__ __forceinline__ uint32_t equal_mask4(uint32_t c, const uint32_t nb[8])
+{
+    uint32_t e[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) e[d] = eq8(nb[d], c);
+    return merge_dirs(e);
+}
+
 // FIX >= 0 fixes the mode word at compile time (the kernels pass the common
 // mode, lambda-thinning with F^- = max, this way); FIX < 0 reads `mode`.
 template <int FIX = -1>
@@ -165,22 +183,17 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
                                            const uint32_t *comp, uint32_t lam, int mode, int &nin)
 {
     uint32_t okacc = 0;
+    uint32_t M = lower_mask4(c, nb);
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
-        uint32_t M;
-        const uint32_t ok = decide4<FIX>(c, nb, vm, comp, lam, mode, M);
+        const uint32_t ok = decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
         if (!ok) break;
-        // alpha^-: largest lower neighbour, by a tree of byte maxima; direction d
-        // of point k is lower iff bit d of byte k of M is set
-#define THIN_LOWER_NB(d) (nb[d] & ((((M >> (d)) & kLsb8) * 0xffu)))
-        const uint32_t alpha =
-            __vmaxu4(__vmaxu4(__vmaxu4(THIN_LOWER_NB(0), THIN_LOWER_NB(1)), __vmaxu4(THIN_LOWER_NB(2), THIN_LOWER_NB(3))),
-                     __vmaxu4(__vmaxu4(THIN_LOWER_NB(4), THIN_LOWER_NB(5)), __vmaxu4(THIN_LOWER_NB(6), THIN_LOWER_NB(7))));
-#undef THIN_LOWER_NB
+        const uint32_t alpha = alpha4(nb, M);
         const uint32_t okm = ok * 0xffu;
         c = (alpha & okm) | (c & ~okm);
         okacc |= ok;
         nin += __popc(ok & in);
+        M &= ~equal_mask4(c, nb);  // unmoved points: no neighbour equal to c is lower
     }
     return okacc;
 }
@@ -201,7 +214,7 @@ __device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb
         c = (alpha & okm) | (c & ~okm);
         okacc |= ok;
         nin += __popc(ok & in);
-        M = lower_mask4(c, nb);
+        M &= ~equal_mask4(c, nb);
         ok = decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
     }
     return okacc;

@@ -78,7 +78,7 @@ struct Ctl {
     int error;
     int steps;
     unsigned list_count[3];
-    int pad;
+    unsigned next_item[3];  // per step (mod 3): items claimed beyond the first one of every warp
 };
 
 // Shared memory of one warp: tile buffer, cell stamps (with a border ring of
@@ -405,10 +405,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
                                     : *reinterpret_cast<volatile unsigned *>(&P.ctl->list_count[s % 3]);
         const unsigned *L = P.lists + size_t(s % 3) * P.total_tiles;
         unsigned *Lnext = P.lists + size_t((s + 1) % 3) * P.total_tiles;
-        if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->list_count[(s + 2) % 3] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {  // counters of step s + 2, last used in step s - 1
+            P.ctl->list_count[(s + 2) % 3] = 0;
+            P.ctl->next_item[(s + 2) % 3] = 0;
+        }
         const int src = s & 1;
         bool failed = false;
-        for (unsigned i = gw; i < count; i += nwarps) {
+        // Every warp takes item gw first, then claims further items one at a time from the step's counter,
+        // so that warps that drew light tiles take more of them and the step ends with the grid together.
+        for (unsigned i = gw; i < count;) {
             int img, tx, ty;
             decode(P, full, L, i, img, tx, ty);
             const ImgDesc &D = P.imgs[img];
@@ -511,7 +516,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
                 atomicAdd(&P.st[img].tested, (unsigned long long)ntest);
                 atomicMax(&P.st[img].last_step, s);
             }
-            __syncwarp();
+            unsigned nxt = 0;
+            if (lane == 0) nxt = nwarps + atomicAdd(&P.ctl->next_item[s % 3], 1u);
+            i = __shfl_sync(0xffffffffu, nxt, 0);
         }
         if (__syncthreads_or(failed)) {
             if (threadIdx.x == 0) atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
@@ -614,7 +621,7 @@ struct TiledPrepared {
 };
 
 int tiled_prepare(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, bool async_alloc,
-                  TiledPrepared **out)
+                  TiledPrepared **out, int max_grid)
 {
     *out = nullptr;
     bool any16 = false;
@@ -788,6 +795,7 @@ int tiled_prepare(const JobSpec *jobs, int n, const thin_options &opt, cudaStrea
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, kThreads, T->smem);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     T->grid = std::max(1, std::min(sms * per_sm, (total_tiles + kWarps - 1) / kWarps));
+    if (max_grid > 0) T->grid = std::min(T->grid, max_grid);
     if (opt.reserved == 1) T->grid = std::max(T->grid, std::min(2, sms * per_sm));
     if (e != cudaSuccess) {
         tiled_release(T, stream);
@@ -897,24 +905,56 @@ int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t 
 // Allocation-free entry point.
 //
 // Some callers cannot allocate device memory at the moment they want to thin
-// an image: an application that owns all device memory through its own fixed
-// budget, or code that runs while another thread of the process is capturing
-// a CUDA graph in global capture mode (where allocation calls are refused).
-// thin_run_noalloc serves them with the tiled engine and no allocation at all:
-// its scratch (the second ping-pong buffer, the change stamps, the worklists
-// and the control words) lives in one fixed array in device memory that the
-// library declares at file scope.  Every GPU that loads the library holds the
-// array until the process exits.
+// an image: an application that hands all device memory to its own allocator
+// at start-up (a further cudaMalloc would fail or eat into that budget), or a
+// loop with a fixed time budget that may not call into the allocator, which
+// can have to map new memory or wait for the device.  thin_run_noalloc serves
+// them with the tiled engine and no allocation at all: its scratch (the
+// second ping-pong buffer, the change stamps, the worklists and the control
+// words) lives in one fixed array in device memory that the library declares
+// at file scope.  Every GPU that loads the library holds the array until the
+// process exits.
 static __device__ __align__(256) unsigned char g_thin_noalloc_scratch[THIN_NOALLOC_SCRATCH_BYTES];
 
 namespace thin {
 namespace {
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_base[256] = {};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (in host code the array's name is only a host-side stand-in).
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;  // context the address belongs to (0: unknown)
+    void *base = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoallocSlot g_noalloc_slot[256];
+
+// Identity of the calling thread's current context, 0 if it cannot be had.
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the scratch array on the current device (in host code the
+// array's name is only a host-side stand-in).  Looked up at the first call on
+// a device, and again only if the device's context has been created anew
+// since (after cudaDeviceReset the array lives at a new address).
 cudaError_t noalloc_scratch(void **base)
 {
     int dev = 0;
@@ -922,13 +962,16 @@ cudaError_t noalloc_scratch(void **base)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
+    NoallocSlot &S = g_noalloc_slot[dev];
+    const unsigned long long id = current_context_id();
+    if (!S.base || id == 0 || id != S.ctx_id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_thin_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_base[dev] = p;
+        S.base = p;
+        S.ctx_id = current_context_id();  // the lookup makes the context current if it was not
     }
-    *base = g_noalloc_base[dev];
+    *base = S.base;
     return cudaSuccess;
 }
 

@@ -2,8 +2,12 @@
 
 Requests of mixed sizes, dtypes and lambdas go through one server from
 several host threads; every result must be bit-exact to what thin_run gives
-the same image alone (integer work), and to the CPU oracle where the oracle
-is quick.  Admission limits (queue cap, budget) are checked too."""
+the same image alone (integer work) and to the CPU oracle.  Each image is
+retired as soon as it is finished, so a slow image does not hold back small
+ones admitted with it.  Admission limits (queue cap, budget) are checked
+too.  Lambda applies to pixel values as given, for u8 and u16 alike."""
+import multiprocessing as mp
+import os
 import threading
 
 import numpy as np
@@ -33,7 +37,7 @@ def mixed_requests(n, seed):
     for k in range(n):
         dt = "u16" if k % 2 else "u8"
         h, w = (int(np.exp(rng.uniform(np.log(8), np.log(600)))) for _ in range(2))
-        lam = int(rng.choice([0, 10])) * (16 if dt == "u16" else 1)
+        lam = int(rng.choice([0, 10]))
         reqs.append((synth.value_noise_image(h, w, dt, seed=seed * 1000 + k), lam))
     # two images too large for one cluster's shared memory (the tiled engine), and two with no interior
     reqs.append((synth.value_noise_image(1500, 1300, "u8", seed=seed + 7), 10))
@@ -41,6 +45,17 @@ def mixed_requests(n, seed):
     reqs.append((synth.value_noise_image(2, 50, "u8", seed=1), 5))
     reqs.append((np.zeros((0, 0), np.uint8), 0))
     return reqs
+
+
+def _oracle(args):
+    img, lam = args
+    return oracle.thin(img, lam)
+
+
+def oracle_all(pairs):
+    """The oracle on every (image, lambda), in a spawn pool (safe after CUDA is initialised)."""
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 2)) as pool:
+        return pool.map(_oracle, pairs, chunksize=1)
 
 
 def collect(srv, n):
@@ -56,7 +71,7 @@ def collect(srv, n):
 
 @pytest.mark.parametrize("slots", [12, 2])
 def test_serve_mix_from_three_threads_equals_alone(slots):
-    """With 2 slots, batches are small and all four lanes run different image sizes at once."""
+    """With 2 slots, batches are small and the lanes run different image sizes at once."""
     reqs = mixed_requests(45, 5 + slots)
     tickets = [None] * len(reqs)
     with thin.Server(1 << 30, max_slots=slots, queue_cap=len(reqs)) as srv:
@@ -70,18 +85,45 @@ def test_serve_mix_from_three_threads_equals_alone(slots):
             t.join()
         got = collect(srv, len(reqs))
     assert sorted(got) == sorted(tickets)
-    for (img, lam), t in zip(reqs, tickets):
+    # the oracle on every image up to 600 x 600 (the two larger ones are checked against thin_run here
+    # and against the oracle at full size elsewhere)
+    real = [k for k, (img, _) in enumerate(reqs) if img.shape[0] >= 3 and img.shape[1] >= 3]
+    small = [k for k in real if reqs[k][0].size <= 600 * 600]
+    orc = dict(zip(small, oracle_all([reqs[k] for k in small])))
+    for k, ((img, lam), t) in enumerate(zip(reqs, tickets)):
         out, st = got[t]
-        if img.shape[0] < 3 or img.shape[1] < 3:
+        if k not in real:
             assert np.array_equal(out, img) and st["converged"] == 1
             continue
         ref, st1 = alone(img, lam)
         assert np.array_equal(out, ref), (img.shape, img.dtype, lam)
         assert st["lowered"] == st1["lowered"] and st["last_change_phase"] == st1["last_change_phase"]
         assert st["converged"] == 1
-        if img.size <= 200 * 200:
-            oref, ost = oracle.thin(img, lam)
+        if k in orc:
+            oref, ost = orc[k]
             assert np.array_equal(out, oref) and st["lowered"] == ost["lowered"]
+            assert st["last_change_phase"] == ost["last_change_phase"]
+
+
+def test_serve_small_images_do_not_wait_for_a_slow_one():
+    """One slow image (512^2, lambda 20, about 4000 phases) and 40 small ones submitted right after it:
+    every small one finishes before the slow one, whether a lane admitted them with it or not."""
+    slow = synth.value_noise_image(512, 512, "u8", seed=38)
+    small = [synth.value_noise_image(48, 64, "u8", seed=100 + k) for k in range(40)]
+    with thin.Server(1 << 30, max_slots=8 * 64, queue_cap=64) as srv:
+        ts = srv.submit(slow, 20)
+        tk = [srv.submit(im, 0) for im in small]
+        order = []
+        while len(order) < 1 + len(small):
+            t = srv.wait_any(20000)
+            assert t is not None
+            done, out, st, rc = srv.poll(t)
+            assert done and rc == 0
+            order.append(t)
+            img, lam = (slow, 20) if t == ts else (small[tk.index(t)], 0)
+            ref, _ = alone(img, lam)
+            assert np.array_equal(out, ref)
+    assert order[-1] == ts
 
 
 def test_serve_queue_cap_and_budget():

@@ -1,11 +1,11 @@
 """The allocation-free entry point, thin_run_noalloc, against thin_run.
 
-thin_run_noalloc exists for callers that cannot allocate device memory (an
-application whose device memory is all handed to its own allocator up front,
-or code running while another thread captures a CUDA graph in global capture
-mode, where allocation calls are refused).  It must give exactly what
-thin_run gives, call after call, although every call reuses one fixed
-scratch array.  This file sorts last so that a run stopping at the first
+thin_run_noalloc exists for callers that cannot allocate device memory when
+they call in (an application whose device memory is all handed to its own
+allocator at start-up, or a loop with a fixed time budget that may not call
+into the allocator).  It must give exactly what thin_run gives, call after
+call, although every call reuses one fixed scratch array, and it must leave
+the device's free memory as it found it.  This file sorts last so that a run stopping at the first
 failure has already run every other test; it also passes on its own."""
 import ctypes
 
@@ -67,9 +67,27 @@ def test_noalloc_unaligned_rows_and_cap():
     assert torch.equal(big, ref)
 
 
+def test_noalloc_allocates_nothing():
+    lib = thin.load()
+    img = synth.value_noise_image(700, 900, "u8", seed=31)
+    t = torch.from_numpy(img).cuda()
+    rc, _ = _call(lib.thin_run_noalloc, t.clone(), 12)  # first call: the module and its array are in place after it
+    assert rc == thin.THIN_OK
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rc, st = _call(lib.thin_run_noalloc, t, 12)
+        assert rc == thin.THIN_OK and st["converged"] == 1
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0  # the driver's free bytes: no allocation by any route
+
+
 def test_noalloc_rejects_images_beyond_its_scratch():
     lib = thin.load()
-    t = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
+    img = synth.value_noise_image(4096, 4096, "u8", seed=32)
+    t = torch.from_numpy(img).cuda()
+    before = t.clone()
     rc, _ = _call(lib.thin_run_noalloc, t, 0)
     assert rc == thin.THIN_ERR_TOO_LARGE
-    assert int(t.sum()) == 0
+    assert torch.equal(t, before)  # rejected: the image is left untouched
