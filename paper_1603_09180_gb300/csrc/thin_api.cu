@@ -85,16 +85,18 @@ int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Groupin
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int spread = 1;
     while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms * (16 / G->nw)) spread *= 2;
-    for (int C = 1; C <= 8; C *= 2) {
-        std::vector<int> idx;
-        for (int k = 0; k < n; ++k) {
-            if (cls[k] <= 0) continue;
-            int c = cls[k];
-            while (c < spread && specs[k].h / (2 * c) >= 32) c *= 2;
-            if (c == C) idx.push_back(k);
+    // one launch per cluster size and element size (the kernel is built for each element size)
+    for (int C = 1; C <= 8; C *= 2)
+        for (int dt = THIN_U8; dt <= THIN_U16; ++dt) {
+            std::vector<int> idx;
+            for (int k = 0; k < n; ++k) {
+                if (cls[k] <= 0 || specs[k].dtype != dt) continue;
+                int c = cls[k];
+                while (c < spread && specs[k].h / (2 * c) >= 32) c *= 2;
+                if (c == C) idx.push_back(k);
+            }
+            if (!idx.empty()) G->resident.push_back({C, idx});
         }
-        if (!idx.empty()) G->resident.push_back({C, idx});
-    }
     // Images too large for a cluster: the wide resident mode (the image held
     // by several clusters of one launch) when at most kWideMax of them are in
     // the call, each then having most of the GPU; the tiled engine otherwise.
@@ -123,8 +125,8 @@ namespace {
 // by side (created once per thread and device, kept until the process exits).
 struct SideStreams {
     int dev = -1;
-    cudaStream_t s[5] = {};
-    cudaEvent_t ev[6] = {};
+    cudaStream_t s[kMaxResidentGroups] = {};
+    cudaEvent_t ev[kMaxResidentGroups + 1] = {};
 };
 
 cudaError_t side_streams(SideStreams **out)

@@ -48,10 +48,8 @@ int naive_run(const JobSpec &job, const thin_options &opt, cudaStream_t stream, 
 int tiled_run(const JobSpec *jobs, int n, const thin_options &opt, cudaStream_t stream, thin_stats *out);
 
 // Resident engine: each image held in the shared memory of one thread-block
-// cluster of C blocks (1, 2, 4 or 8) of nw warps (4, 8 or 16; 16 / nw blocks
-// share an SM) for its whole run.
-int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream,
-                 thin_stats *out);
+// cluster of C blocks (1, 2, 4 or 8) of 16 warps, one block per SM, for its
+// whole run; one launch per cluster size and element size.
 // Device-side records of the resident engine (thin_resident.cu).
 struct ResJob {
     unsigned long long img;    // the caller's image, thinned in place
@@ -118,7 +116,7 @@ struct ResArgs {
 // be enqueued any number of times: see resident_prepare / _enqueue /
 // _collect / _release.
 struct ResidentPrepared {
-    int n = 0, C = 0, nw = 0, grid = 0, strips = 0;
+    int n = 0, C = 0, nw = 0, grid = 0, strips = 0, es = 1;
     size_t smem = 0;
     bool async_alloc = true;
     char *base = nullptr;         // one device allocation holding everything below
@@ -160,6 +158,11 @@ void tiled_release(TiledPrepared *T, cudaStream_t stream);
 void tiled_defaults(int dtype, int *tw, int *th, int *halo);
 
 int cuda_status(cudaError_t e);
+
+// Resident launch groups of a batch at most: one per cluster size (1, 2, 4,
+// 8) and element size (u8, u16).  Execution::enqueue needs that many helper
+// streams, and one event more.
+constexpr int kMaxResidentGroups = 8;
 
 // Launch groups of a batch: (cluster size, job indices) for the resident
 // engine, job indices for the tiled engine.

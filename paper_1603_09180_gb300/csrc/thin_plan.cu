@@ -99,8 +99,8 @@ int thin_plan_create(const thin_job *jobs, int n, thin_adj adj, const thin_optio
         return rc;
     }
     cudaStream_t cs = nullptr;
-    std::vector<cudaStream_t> side(4, nullptr);
-    std::vector<cudaEvent_t> ev(5, nullptr);
+    std::vector<cudaStream_t> side(kMaxResidentGroups, nullptr);
+    std::vector<cudaEvent_t> ev(kMaxResidentGroups + 1, nullptr);
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     p->stream = cs;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);

@@ -182,7 +182,8 @@ __device__ __forceinline__ void or_word(uint32_t *bits, int key, uint32_t m)
     if (key >= 0) atomicOr(bits + key, m);
 }
 
-template <int NW>
+// ES: element size of every image of the launch (1: u8, 2: u16).
+template <int NW, int ES>
 __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -226,9 +227,9 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             if (job >= P.njobs) break;
         }
         const ResJob J = P.jobs[job];
-        const int es = J.dtype == THIN_U16 ? 2 : 1;
+        constexpr int es = ES;
         const int mode = P.rule | (J.adj << 2);      // F^- reading, operator, adjacency pair
-        const bool simd = es == 1 && J.adj == 0;     // u8 under (8,4): four points at once
+        const bool simd = J.adj == 0;                // (8,4): four points at once (bytes for u8, 16-bit lanes for u16)
         const uint32_t *ptab = tabs + (J.adj ? kTabOffset48 : 0);
         const int R = J.rows, HR = J.hr, RP = J.rp, CW = J.cw, WPR = J.wpr;
         const int LR = R + 2 * HR;   // shared rows: HR halo rows, R own rows, HR halo rows
@@ -345,6 +346,35 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                     in = (y >= row0 && y < row0 + R) ? vm : 0u;  // own points count
                 };
                 bool moved_own = false;
+                // the (8,4) point test on four points at once, in the common mode's own build where it applies
+                auto test_item = [&](const uint8_t *rb, int pxx, uint32_t vm) -> uint32_t {
+                    if constexpr (ES == 1) {
+                        return (kFix && mode == 0) ? test_u8<0>(rb - RP, rb, rb + RP, pxx, vm, comp, J.lam, mode)
+                                                   : test_u8(rb - RP, rb, rb + RP, pxx, vm, comp, J.lam, mode);
+                    } else {
+                        const uint16_t *r16 = reinterpret_cast<const uint16_t *>(rb);
+                        const int rp16 = RP / 2;
+                        return (kFix && mode == 0) ? test_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, comp, J.lam, mode)
+                                                   : test_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, comp, J.lam, mode);
+                    }
+                };
+                // the lowering loop on four points (ok: a first test's result, or ~0u to test first)
+                auto lower_item = [&](uint8_t *rb, int pxx, uint32_t vm, uint32_t in, uint32_t ok) -> uint32_t {
+                    if constexpr (ES == 1) {
+                        if (ok == ~0u)
+                            return (kFix && mode == 0) ? item_u8<0>(rb - RP, rb, rb + RP, pxx, vm, in, comp, J.lam, mode, nlow)
+                                                       : item_u8(rb - RP, rb, rb + RP, pxx, vm, in, comp, J.lam, mode, nlow);
+                        return (kFix && mode == 0)
+                                   ? item_u8_tested<0>(rb - RP, rb, rb + RP, pxx, vm, in, ok, comp, J.lam, mode, nlow)
+                                   : item_u8_tested(rb - RP, rb, rb + RP, pxx, vm, in, ok, comp, J.lam, mode, nlow);
+                    } else {
+                        uint16_t *r16 = reinterpret_cast<uint16_t *>(rb);
+                        const int rp16 = RP / 2;
+                        return (kFix && mode == 0)
+                                   ? item_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, comp, J.lam, mode, nlow)
+                                   : item_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, comp, J.lam, mode, nlow);
+                    }
+                };
                 // A scan round: each warp takes the bitmap words warp, warp + NW, ... of this parity
                 // (one per lane), consumes their bits and appends the groups it found to the block's
                 // queue.  After a block barrier the queue is split evenly over the warps, and each
@@ -411,19 +441,18 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                     ntest += __popc(in);
                                     uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
                                     if (simd) {
-                                        const uint32_t okb =
-                                            (kFix && mode == 0) ? test_u8<0>(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode)
-                                                                : test_u8(rb - RP, rb, rb + RP, px, vm, comp, J.lam, mode);
+                                        const uint32_t okb = test_item(rb, px, vm);
                                         lowers = okb != 0;
                                         code |= int((okb | (okb >> 7) | (okb >> 14) | (okb >> 21)) & 0xfu) << 16;
                                     } else {
-                                        tmoved = es == 2 ? item_table<uint16_t>(
-                                                               reinterpret_cast<const uint16_t *>(rb - RP),
-                                                               reinterpret_cast<uint16_t *>(rb),
-                                                               reinterpret_cast<const uint16_t *>(rb + RP), px, vm, in,
-                                                               ptab, J.lam, mode, nlow)
-                                                         : item_table<uint8_t>(rb - RP, rb, rb + RP, px, vm, in, ptab,
-                                                                               J.lam, mode, nlow);
+                                        if constexpr (ES == 2)
+                                            tmoved = item_table<uint16_t>(reinterpret_cast<const uint16_t *>(rb - RP),
+                                                                          reinterpret_cast<uint16_t *>(rb),
+                                                                          reinterpret_cast<const uint16_t *>(rb + RP), px,
+                                                                          vm, in, ptab, J.lam, mode, nlow);
+                                        else
+                                            tmoved = item_table<uint8_t>(rb - RP, rb, rb + RP, px, vm, in, ptab, J.lam,
+                                                                         mode, nlow);
                                         if (tmoved & in) moved_own = true;
                                     }
                                 }
@@ -449,17 +478,13 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                 uint32_t vm, in;
                                 where(code, gcr, gcc, vm, in);
                                 if (nq <= kTwoPass) ntest += __popc(in);
-                                uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + gcc * 8;
+                                uint8_t *rb = rows_base + size_t(2 * gcr + py) * RP + 16 + size_t(8 * es) * gcc;
                                 if (kOkPass && nq > kTwoPass) {  // tested in the first pass: start lowering at once
                                     const uint32_t o4 = wok[k];
                                     const uint32_t okb = (o4 & 1u) | ((o4 & 2u) << 7) | ((o4 & 4u) << 14) | ((o4 & 8u) << 21);
-                                    moved = (kFix && mode == 0)
-                                                ? item_u8_tested<0>(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow)
-                                                : item_u8_tested(rb - RP, rb, rb + RP, px, vm, in, okb, comp, J.lam, mode, nlow);
+                                    moved = lower_item(rb, px, vm, in, okb);
                                 } else {
-                                    moved = (kFix && mode == 0)
-                                                ? item_u8<0>(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow)
-                                                : item_u8(rb - RP, rb, rb + RP, px, vm, in, comp, J.lam, mode, nlow);
+                                    moved = lower_item(rb, px, vm, in, ~0u);
                                 }
                                 if (moved & in) moved_own = true;
                             }
@@ -632,12 +657,12 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
     }
 }
 
-// Launch shape of k_resident<NW>: as many clusters of C blocks as fit at
+// Launch shape of k_resident<NW, ES>: as many clusters of C blocks as fit at
 // once (each loops over the job queue), at most one per job.
-template <int NW>
+template <int NW, int ES>
 cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
 {
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_resident<NW>));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_resident<NW, ES>));
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cudaLaunchAttribute attr[1];
@@ -651,7 +676,7 @@ cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<NW>, &cfg);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&clusters, k_resident<NW, ES>, &cfg);
     if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
     *grid = C * std::min(clusters, n);
     return e;
@@ -659,7 +684,7 @@ cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
 
 // Wide launches are cooperative: the clusters of one image wait on one
 // another at every step, so all of them must be resident at once.
-template <int NW>
+template <int NW, int ES>
 cudaError_t resident_launch(int C, int grid, size_t smem, cudaStream_t stream, const ResArgs &P)
 {
     cudaLaunchConfig_t cfg;
@@ -677,7 +702,14 @@ cudaError_t resident_launch(int C, int grid, size_t smem, cudaStream_t stream, c
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = P.strips > 0 ? 2 : 1;
-    return cudaLaunchKernelEx(&cfg, k_resident<NW>, P);
+    return cudaLaunchKernelEx(&cfg, k_resident<NW, ES>, P);
+}
+
+// The launch shape for blocks of nw warps (16: the one shape the engine uses) and element size es.
+cudaError_t resident_shape_for(int nw, int es, int C, int n, size_t smem, int *grid)
+{
+    if (nw != kResMaxWarps) return cudaErrorInvalidValue;
+    return es == 2 ? resident_shape<kResMaxWarps, 2>(C, n, smem, grid) : resident_shape<kResMaxWarps, 1>(C, n, smem, grid);
 }
 
 }  // namespace
@@ -726,12 +758,7 @@ int resident_wide_strips(int w, int h, int dtype, size_t smem_limit, int nw, int
             if (smem > smem_limit) continue;
             // every cluster of the launch must be resident at once
             int grid = 0;
-            cudaError_t e;
-            switch (nw) {
-            case 4: e = resident_shape<4>(C, S, smem, &grid); break;
-            case 8: e = resident_shape<8>(C, S, smem, &grid); break;
-            default: e = resident_shape<16>(C, S, smem, &grid); break;
-            }
+            const cudaError_t e = resident_shape_for(nw, es, C, S, smem, &grid);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
@@ -772,7 +799,10 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     R->async_alloc = async_alloc;
     if (strips > 0 && n != 1) return THIN_ERR_ARG;  // a wide launch runs one image
     const int B = strips > 0 ? strips * C : C;      // blocks per image
-    if (nw != 4 && nw != 8 && nw != 16) return THIN_ERR_ARG;
+    if (nw != kResMaxWarps || n < 1) return THIN_ERR_ARG;
+    R->es = elem_size(jobs[0].dtype);
+    for (int k = 1; k < n; ++k)
+        if (elem_size(jobs[k].dtype) != R->es) return THIN_ERR_ARG;  // one element size per launch
     const size_t limit = resident_smem_limit(kResMaxWarps / nw);
     std::vector<ResJob> rj(n);
     size_t smem = 0;
@@ -870,11 +900,7 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
     if (e == cudaSuccess) {
         const int want = strips > 0 ? strips : n;  // clusters wanted
-        switch (nw) {
-        case 4: e = resident_shape<4>(C, want, smem, &R->grid); break;
-        case 8: e = resident_shape<8>(C, want, smem, &R->grid); break;
-        default: e = resident_shape<16>(C, want, smem, &R->grid); break;
-        }
+        e = resident_shape_for(nw, R->es, C, want, smem, &R->grid);
         if (e == cudaSuccess && strips > 0 && R->grid < B) return THIN_ERR_ARG;  // not all strips fit at once
     }
     return e == cudaSuccess ? THIN_OK : cuda_status(e);
@@ -887,11 +913,8 @@ cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream)
     cudaError_t e = cudaMemcpyAsync(R.P.st, R.st0, R.st_bytes, cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.P.ctl, R.ctl0, sizeof(ResCtl), cudaMemcpyDeviceToDevice, stream);
     if (e != cudaSuccess) return e;
-    switch (R.nw) {
-    case 4: return resident_launch<4>(R.C, R.grid, R.smem, stream, R.P);
-    case 8: return resident_launch<8>(R.C, R.grid, R.smem, stream, R.P);
-    default: return resident_launch<16>(R.C, R.grid, R.smem, stream, R.P);
-    }
+    return R.es == 2 ? resident_launch<kResMaxWarps, 2>(R.C, R.grid, R.smem, stream, R.P)
+                     : resident_launch<kResMaxWarps, 1>(R.C, R.grid, R.smem, stream, R.P);
 }
 
 // Waits for the stream and writes the stats of job k (the caller's order) to out[k].
@@ -934,31 +957,6 @@ void resident_release(ResidentPrepared &R, cudaStream_t stream)
         else cudaFree(R.base);
     }
     R.base = nullptr;
-}
-
-// Runs the jobs (all fitting cluster size C with nw warps a block) in one launch of k_resident.
-int resident_run(const JobSpec *jobs, int n, int C, int nw, const thin_options &opt, cudaStream_t stream, thin_stats *out)
-{
-    if (n <= 0) return THIN_OK;
-    if (opt.max_phases == 0) {
-        if (out)
-            for (int k = 0; k < n; ++k) {
-                std::memset(&out[k], 0, sizeof out[k]);
-                out[k].status = THIN_ERR_NOT_CONVERGED;
-                out[k].last_change_phase = -1;
-                out[k].end_phase = opt.start_phase;
-            }
-        return THIN_ERR_NOT_CONVERGED;
-    }
-    ResidentPrepared R;
-    int rc = resident_prepare(jobs, n, C, nw, opt, stream, true, &R);
-    if (rc == THIN_OK) {
-        const cudaError_t e = resident_enqueue(R, stream);
-        if (e != cudaSuccess) rc = cuda_status(e);
-        else if (out) rc = resident_collect(R, opt, stream, out);
-    }
-    resident_release(R, stream);
-    return rc;
 }
 
 }  // namespace thin

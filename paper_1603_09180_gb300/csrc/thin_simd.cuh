@@ -120,10 +120,14 @@ __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], ui
     return decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
 }
 
-// decide4 with the lower masks M of the centre values c already computed.
-template <int FIX>
-__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                             uint32_t lam, int mode_rt, uint32_t M)
+// The decision of Sec. 2.1 from masks alone (bit d of byte k: direction d of
+// point k): M the lower neighbours, and below() the neighbours below
+// F(x) - lambda (none when F(x) <= lambda), computed only when the lambda rule
+// or the skeleton's test needs it.  The test depends on the pixel values
+// through these two masks only.
+template <int FIX, typename Below>
+__device__ __forceinline__ uint32_t decide_masks(uint32_t M, uint32_t vm, const uint32_t *comp, uint32_t lam,
+                                                 int mode_rt, Below below)
 {
     const int mode = FIX >= 0 ? FIX : mode_rt;
     const int rule = mode & 1;
@@ -134,15 +138,12 @@ __device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], u
     const uint32_t nzt = nonzero8(t);
     uint32_t ok = ((nonzero8(st) & ~nzt) >> 7) & vm;          // destructible
     const uint32_t dv = (nzt >> 7) & vm;                      // k-divergent
+    uint32_t D = 0;
+    bool haveD = false;
     if (lam != 0 && dv) {
-        // deep lower neighbours: value < F(x) - lambda (none when F(x) <= lambda)
-        const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
-        const uint32_t cl = __vsubus4(c, lrep);
-        const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
-        uint32_t dp[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
-        const uint32_t deep = merge_dirs(dp) & mc;
+        D = below();
+        haveD = true;
+        const uint32_t deep = D & mc;
         // F^- = max: a component fails when no member is shallow (value >= F(x) - lambda);
         // F^- = min: a component fails when some member is deep
         const uint32_t probe = rule == 0 ? (mc & ~deep) : deep;
@@ -158,19 +159,30 @@ __device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], u
     }
     if (mode & 2) {
         // shallow: some lower neighbour >= F(x) - lambda, i.e. F(x) - alpha^- <= lambda
-        const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
-        const uint32_t cl = __vsubus4(c, lrep);
-        const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
-        uint32_t dp[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
-        const uint32_t shallow = nonzero8(M & ~merge_dirs(dp));
+        if (!haveD) D = below();
+        const uint32_t shallow = nonzero8(M & ~D);
         const uint32_t U = ~M;                                   // neighbours >= F(x), per byte
         const uint32_t peak = ~nonzero8(U) & kMsb8;              // none: T+ = 0
         const uint32_t end = nonzero8(U) & ~nonzero8(U & ((U | kMsb8) - kLsb8));  // exactly one
         ok = (ok | ((peak & shallow) >> 7)) & ~((end & ~shallow) >> 7) & vm;
     }
     return ok & 0x01010101u;
+}
+
+// decide4 with the lower masks M of the centre values c already computed.
+template <int FIX>
+__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
+                                             uint32_t lam, int mode_rt, uint32_t M)
+{
+    return decide_masks<FIX>(M, vm, comp, lam, mode_rt, [&] {
+        const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
+        const uint32_t cl = __vsubus4(c, lrep);
+        const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
+        uint32_t dp[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) dp[d] = lt8(nb[d], cl, cll, clh);
+        return merge_dirs(dp);
+    });
 }
 
 // The lowering loop of Sec. 2.2 on the four points: while a point is
@@ -338,11 +350,200 @@ __device__ __forceinline__ uint32_t item_table(const T *ra, T *rb, const T *rc, 
     return moved;
 }
 
-__device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px,
-                                             uint32_t vm, uint32_t in, const uint32_t *tab, uint32_t lam, int mode,
+// ---------------------------------------------------------------------------
+// u16 images under (8,4): the same four points, two per 32-bit word in 16-bit
+// lanes (word A holds points 0 and 1, word B points 2 and 3).  The pixel
+// comparisons run per lane; their results are brought to the byte-per-point
+// mask format, and the decision is decide_masks, as for u8.
+
+constexpr uint32_t kMsb16 = 0x80008000u;
+
+// Two unsigned 16-bit comparisons a < b at once: bit 15 of each lane set where
+// lane(a) < lane(b) (the borrow trick of lt8 on 16-bit lanes).
+__device__ __forceinline__ uint32_t lt16(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;
+    const uint32_t r = (a | kMsb16) - (b & 0x7fff7fffu);
+    const uint32_t dh = (r ^ ~x) & kMsb16;
+    return (x & b & kMsb16) | (~x & dh);
+}
+
+// Bit 15 of each lane set where the lanes of a and b are equal.
+__device__ __forceinline__ uint32_t eq16(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;
+    return ~(((x & 0x7fff7fffu) + 0x7fff7fffu) | x) & kMsb16;
+}
+
+// Lane results of words A and B (bit 15 per lane) as bit 7 of bytes 0..3.
+__device__ __forceinline__ uint32_t lanes_to_bytes(uint32_t a, uint32_t b)
+{
+    return __byte_perm(a, b, 0x7531) & kMsb8;
+}
+
+struct Px16 {
+    uint32_t nbA[8], nbB[8];  // neighbours in ring order, per word
+    uint32_t cA, cB;          // centre values
+};
+
+// Masks of the neighbours below the centre values (byte k = point k).
+__device__ __forceinline__ uint32_t lower_mask16(const Px16 &P, uint32_t cA, uint32_t cB)
+{
+    uint32_t lt[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) lt[d] = lanes_to_bytes(lt16(P.nbA[d], cA), lt16(P.nbB[d], cB));
+    return merge_dirs(lt);
+}
+
+__device__ __forceinline__ uint32_t equal_mask16(const Px16 &P)
+{
+    uint32_t e[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) e[d] = lanes_to_bytes(eq16(P.nbA[d], P.cA), eq16(P.nbB[d], P.cB));
+    return merge_dirs(e);
+}
+
+// Per-lane masks (0xffff) of the points whose byte in m is 0x01.
+__device__ __forceinline__ uint32_t lanes_of_bytes_lo(uint32_t m) { return __byte_perm(m, 0, 0x1100) * 0xffu; }
+__device__ __forceinline__ uint32_t lanes_of_bytes_hi(uint32_t m) { return __byte_perm(m, 0, 0x3322) * 0xffu; }
+
+// alpha^- of the four points: the largest lower neighbour, per lane.
+__device__ __forceinline__ void alpha16(const Px16 &P, uint32_t M, uint32_t &aA, uint32_t &aB)
+{
+    aA = 0;
+    aB = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const uint32_t t = (M >> d) & kLsb8;
+        aA = __vmaxu2(aA, P.nbA[d] & lanes_of_bytes_lo(t));
+        aB = __vmaxu2(aB, P.nbB[d] & lanes_of_bytes_hi(t));
+    }
+}
+
+template <int FIX>
+__device__ __forceinline__ uint32_t decide16m(const Px16 &P, uint32_t vm, const uint32_t *comp, uint32_t lam, int mode,
+                                              uint32_t M)
+{
+    return decide_masks<FIX>(M, vm, comp, lam, mode, [&] {
+        const uint32_t lrep = (lam > 65535u ? 65535u : lam) * 0x00010001u;
+        return lower_mask16(P, __vsubus2(P.cA, lrep), __vsubus2(P.cB, lrep));
+    });
+}
+
+// The lowering loop on the four points (u16).  ok: the result of a first test
+// already made at the current values, or ~0u to test first.  Returns the bytes
+// lowered (0x01 each); P.cA, P.cB receive the new values.
+template <int FIX>
+__device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, uint32_t ok, const uint32_t *comp,
+                                            uint32_t lam, int mode, int &nin)
+{
+    uint32_t okacc = 0;
+    uint32_t M = lower_mask16(P, P.cA, P.cB);
+    if (ok == ~0u) ok = decide16m<FIX>(P, vm, comp, lam, mode, M);
+#pragma unroll 1
+    for (int it = 0; it < 9; ++it) {
+        if (!ok) break;
+        uint32_t aA, aB;
+        alpha16(P, M, aA, aB);
+        const uint32_t mA = lanes_of_bytes_lo(ok), mB = lanes_of_bytes_hi(ok);
+        P.cA = (aA & mA) | (P.cA & ~mA);
+        P.cB = (aB & mB) | (P.cB & ~mB);
+        okacc |= ok;
+        nin += __popc(ok & in);
+        M &= ~equal_mask16(P);  // unmoved points: no neighbour equal to c is lower
+        ok = decide16m<FIX>(P, vm, comp, lam, mode, M);
+    }
+    return okacc;
+}
+
+// Gathers a u16 work item: ra, rb, rc point at the 8-pixel, 16-byte aligned
+// block in rows y - 1, y, y + 1; the pixel just left (px == 0) or just right
+// (px == 1) of each block must be readable.  wb receives row y's block.
+__device__ __forceinline__ void gather_u16(const uint16_t *ra, const uint16_t *rb, const uint16_t *rc, int px, Px16 &P,
+                                           uint4 &wb)
+{
+    // per row: even pixels (0,2) (4,6), odd (1,3) (5,7), and the shifted pairs (-1,1) (3,5) or (2,4) (6,8)
+    uint32_t ev[3][2], od[3][2], sh[3][2];
+    const uint16_t *rows[3] = {ra, rb, rc};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(rows[r]);
+        if (r == 1) wb = w;
+        ev[r][0] = __byte_perm(w.x, w.y, 0x5410);
+        ev[r][1] = __byte_perm(w.z, w.w, 0x5410);
+        od[r][0] = __byte_perm(w.x, w.y, 0x7632);
+        od[r][1] = __byte_perm(w.z, w.w, 0x7632);
+        if (px == 0) {
+            const uint32_t L = *reinterpret_cast<const uint32_t *>(rows[r] - 2);  // pixels -2, -1
+            sh[r][0] = __byte_perm(L, w.x, 0x7632);                             // (-1, 1)
+            sh[r][1] = __byte_perm(w.y, w.z, 0x7632);                           // (3, 5)
+        } else {
+            const uint32_t R = *reinterpret_cast<const uint32_t *>(rows[r] + 8);  // pixels 8, 9
+            sh[r][0] = __byte_perm(w.y, w.z, 0x5410);                           // (2, 4)
+            sh[r][1] = __byte_perm(w.w, R, 0x5410);                             // (6, 8)
+        }
+    }
+    // px == 0: points at the even pixels, E = odd, W = shifted left; px == 1: points at the odd
+    // pixels, E = shifted right, W = even.  Ring order E, NE, N, NW, W, SW, S, SE.
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t *nb = h ? P.nbB : P.nbA;
+        const uint32_t ctr0 = px ? od[0][h] : ev[0][h], ctr1 = px ? od[1][h] : ev[1][h], ctr2 = px ? od[2][h] : ev[2][h];
+        const uint32_t e0 = px ? sh[0][h] : od[0][h], e1 = px ? sh[1][h] : od[1][h], e2 = px ? sh[2][h] : od[2][h];
+        const uint32_t w0 = px ? ev[0][h] : sh[0][h], w1 = px ? ev[1][h] : sh[1][h], w2 = px ? ev[2][h] : sh[2][h];
+        nb[0] = e1;
+        nb[1] = e0;
+        nb[2] = ctr0;
+        nb[3] = w0;
+        nb[4] = w1;
+        nb[5] = w2;
+        nb[6] = ctr2;
+        nb[7] = e2;
+        (h ? P.cB : P.cA) = ctr1;
+    }
+}
+
+// Writes the four points' values back into row y's block.
+__device__ __forceinline__ void store_u16(uint16_t *rb, int px, const Px16 &P, uint4 w)
+{
+    if (px == 0) {
+        w.x = __byte_perm(P.cA, w.x, 0x7610);
+        w.y = __byte_perm(P.cA, w.y, 0x7632);
+        w.z = __byte_perm(P.cB, w.z, 0x7610);
+        w.w = __byte_perm(P.cB, w.w, 0x7632);
+    } else {
+        w.x = __byte_perm(w.x, P.cA, 0x5410);
+        w.y = __byte_perm(w.y, P.cA, 0x7610);
+        w.z = __byte_perm(w.z, P.cB, 0x5410);
+        w.w = __byte_perm(w.w, P.cB, 0x7610);
+    }
+    *reinterpret_cast<uint4 *>(rb) = w;
+}
+
+// One u16 work item under (8,4), tested only: 0x01 in the bytes of the points that would be lowered now.
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t test_u16(const uint16_t *ra, const uint16_t *rb, const uint16_t *rc, int px,
+                                             uint32_t vm, const uint32_t *comp, uint32_t lam, int mode)
+{
+    Px16 P;
+    uint4 w;
+    gather_u16(ra, rb, rc, px, P, w);
+    return decide16m<FIX>(P, vm, comp, lam, mode, lower_mask16(P, P.cA, P.cB));
+}
+
+// One u16 work item under (8,4), lowered (ok: a first test's result, or ~0u);
+// the block is written back if a point moved.
+template <int FIX = -1>
+__device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px, uint32_t vm,
+                                             uint32_t in, uint32_t ok, const uint32_t *comp, uint32_t lam, int mode,
                                              int &nin)
 {
-    return item_table<uint16_t>(ra, rb, rc, px, vm, in, tab, lam, mode, nin);
+    Px16 P;
+    uint4 w;
+    gather_u16(ra, rb, rc, px, P, w);
+    const uint32_t moved = lower16<FIX>(P, vm, in, ok, comp, lam, mode, nin);
+    if (moved) store_u16(rb, px, P, w);
+    return moved;
 }
 
 }  // namespace thin

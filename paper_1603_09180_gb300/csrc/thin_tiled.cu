@@ -311,6 +311,10 @@ __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_
                 moved = item_u8(reinterpret_cast<const uint8_t *>(rb - bw), reinterpret_cast<uint8_t *>(rb),
                                 reinterpret_cast<const uint8_t *>(rb + bw), px, vm, in, tabs + 256, V.lam, V.rule,
                                 nlow);
+            else if (sizeof(T) == 2 && !(V.rule & 4))  // u16 under (8,4): four points in 16-bit lanes
+                moved = item_u16(reinterpret_cast<const uint16_t *>(rb - bw), reinterpret_cast<uint16_t *>(rb),
+                                 reinterpret_cast<const uint16_t *>(rb + bw), px, vm, in, ~0u, tabs + 256, V.lam,
+                                 V.rule, nlow);
             else
                 moved = item_table<T>(rb - bw, rb, rb + bw, px, vm, in, tabs + ((V.rule & 4) ? kTabOffset48 : 0), V.lam,
                                       V.rule, nlow);
@@ -362,7 +366,7 @@ __device__ __forceinline__ void decode(const EngineArgs &P, bool full, const uns
 
 constexpr int kSmemTabs = 4 * kTabWords;  // point and component tables of (8,4) and (4,8), 256 x u32 each
 
-__global__ void __launch_bounds__(kThreads, 4) k_engine(EngineArgs P)
+__global__ void __launch_bounds__(kThreads, 2) k_engine(EngineArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // TMA destinations want 128-byte aligned shared addresses
