@@ -67,7 +67,10 @@ typedef enum { THIN_ADJ_8_4 = 0, THIN_ADJ_4_8 = 1 } thin_adj;
 
 /* Reading of F^-(c) in the lambda rule (Sec. 2.1 leaves F^- undefined):
  * THIN_RULE_MAX takes the largest value of F over the component c (default),
- * THIN_RULE_MIN the smallest. */
+ * THIN_RULE_MIN the smallest.  THIN_RULE_MIN is an unpinned reading: the
+ * paper fixes no example that tells the two apart (they agree on components
+ * of one value), so its results are checked against the oracle's same
+ * reading only. */
 typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
 
 /* The operator (Sec. 2.1-2.2), both lowering points to alpha^-(x, F) in the
