@@ -23,8 +23,9 @@
 //
 // Work in a phase.  Each warp scans its share of the parity's bitmap words
 // and appends the groups it finds to one queue of the block; after a block
-// barrier the queue is split evenly over the warps, so a front that crosses
-// only part of the image still keeps every warp busy.  A warp whose share is
+// barrier the queue is split evenly over ceil(N / 32) warps (at most all 16),
+// so a front that crosses only part of the image still keeps the block's
+// schedulers busy, and a sparse phase runs on full lanes of a few warps.  A warp whose share is
 // larger than 32 groups tests them all first, packing those that lower (with
 // their test result) to the front of its share, then lowers them on full
 // lanes starting from that result; with fewer it tests and lowers in one
@@ -419,8 +420,12 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                     const int N = int(*reinterpret_cast<volatile unsigned *>(&ctrl->qn[qround & 1]));
                     if (tid == 0) ctrl->qn[(qround + 1) & 1] = 0u;  // last read in the previous round
                     ++qround;
-                    const int qa = (N * warp) / NW;
-                    const int nq = (N * (warp + 1)) / NW - qa;  // this warp's share: queue slots qa .. qa + nq - 1
+                    // The shares go to as few warps as give every warp a full chunk of 32 (all 16 when
+                    // there are more than 512 groups): a sparse phase then issues its groups on full
+                    // lanes from about one warp per scheduler instead of a few lanes of every warp.
+                    const int act = min(NW, (N + 31) >> 5);
+                    const int qa = warp < act ? (N * warp) / act : N;
+                    const int nq = warp < act ? (N * (warp + 1)) / act - qa : 0;  // queue slots qa .. qa + nq - 1
                     uint16_t *wqueue = bqueue + qa;
                     uint8_t *wok = bok + qa;
                     if (nq > 0) {
