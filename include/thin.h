@@ -83,8 +83,9 @@ typedef enum { THIN_RULE_MAX = 0, THIN_RULE_MIN = 1 } thin_rule;
 typedef enum { THIN_OP_THINNING = 0, THIN_OP_SKELETON = 1 } thin_op;
 
 /* Kernel family.  RESIDENT holds each image in shared memory for its whole
- * run: in one thread-block cluster (images up to about 1.25 MB: 1120 x 1120
- * u8, 816 x 816 u16), or, in the wide mode, in several clusters of one
+ * run: in one thread-block cluster of up to 16 blocks (images up to about
+ * 2.4 MB: 1550 x 1550 u8, 1100 x 1100 u16; 1.25 MB where the device runs
+ * clusters of 8 at most), or, in the wide mode, in several clusters of one
  * cooperative launch (one block per SM, clusters of 8, 4, 2 or 1 blocks,
  * whichever lets every strip be resident) that exchange boundary rows every
  * 8 phases: images up to about 30 MB.  TILED streams 64 x 32 tiles through

@@ -86,7 +86,7 @@ int group_jobs(const std::vector<JobSpec> &specs, const thin_options &o, Groupin
     int spread = 1;
     while (eligible > 0 && spread < 8 && spread * 2 * eligible <= sms * (16 / G->nw)) spread *= 2;
     // one launch per cluster size and element size (the kernel is built for each element size)
-    for (int C = 1; C <= 8; C *= 2)
+    for (int C = 1; C <= 16; C *= 2)
         for (int dt = THIN_U8; dt <= THIN_U16; ++dt) {
             std::vector<int> idx;
             for (int k = 0; k < n; ++k) {

@@ -137,6 +137,8 @@ void resident_release(ResidentPrepared &R, cudaStream_t stream);
 // Smallest cluster of nw-warp blocks whose shared memory holds a w x h image
 // of `dtype`, 0 if none.
 int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, int *rows_out, int *rp_out);
+// Largest resident cluster on the current device: 16 where it can run, else 8.
+int resident_max_cluster(int nw, size_t smem_limit);
 // Shared memory one block may take when `blocks` blocks share an SM.
 size_t resident_smem_limit(int blocks);
 // Wide mode: the fewest strips (clusters of *c_out blocks of nw warps, the
@@ -160,9 +162,9 @@ void tiled_defaults(int dtype, int *tw, int *th, int *halo);
 int cuda_status(cudaError_t e);
 
 // Resident launch groups of a batch at most: one per cluster size (1, 2, 4,
-// 8) and element size (u8, u16).  Execution::enqueue needs that many helper
+// 8, 16) and element size (u8, u16).  Execution::enqueue needs that many helper
 // streams, and one event more.
-constexpr int kMaxResidentGroups = 8;
+constexpr int kMaxResidentGroups = 10;
 
 // Launch groups of a batch: (cluster size, job indices) for the resident
 // engine, job indices for the tiled engine.

@@ -74,15 +74,16 @@ __device__ const PointTable d_res_component_table48 = kComponentTable48;
 // Shared-memory map of one block for a job.
 constexpr int kOffTabs = 0;      // point and component tables of (8,4) and (4,8), 4 KiB
 constexpr int kOffCtrl = 4096;   // control words
-constexpr int kOffBar = 4224;    // mbarrier of the row staging
-constexpr int kOffRows = 4352;   // image rows (16-byte aligned)
+constexpr int kOffBar = 4352;    // mbarrier of the row staging
+constexpr int kOffRows = 4480;   // image rows (16-byte aligned)
+constexpr int kResMaxCluster = 16;  // largest cluster (16 is a non-portable size, used where the device allows)
 
 struct Ctrl {
     int job;
     long long last;     // last phase in which this block lowered a point, -1 if none
     unsigned long long nlow;
     unsigned long long ntest;
-    long long peer_last[8];  // every block's `last`, pushed by the blocks themselves each phase
+    long long peer_last[kResMaxCluster];  // every block's `last`, pushed by the blocks themselves each phase
     int bar_ok;              // result of the last grid barrier (wide launches)
     unsigned qn[2];          // fill counters of the block's group queue, alternating by scan round
     unsigned fail[2];        // wide launches, cluster leader: a block's grid-barrier wait failed (by step parity)
@@ -95,9 +96,9 @@ __host__ __device__ inline size_t res_queue_off(int rows, int rp, int wpr)
 {
     return res_bits_off(rows, rp) + size_t(4) * 4 * (rows / 2) * wpr;
 }
-// In each round of 32 x nw bitmap words, warp w of nw scans the words
-// w, w + nw, w + 2 nw, ... (one per lane) and queues the groups it finds in a
-// queue of its own: at most 32 words of 32 groups.
+// A scan round covers min(words, 32 nw) bitmap words of 32 groups each, and
+// the block's queue holds every group one round can find: nw x this many
+// entries (32 groups per word times min(ceil(words / nw), 32) words).
 __host__ __device__ inline int res_warp_queue(int rows, int wpr, int nw)
 {
     const int words = (rows / 2) * wpr;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             ctrl->fail[0] = 0u;
             ctrl->fail[1] = 0u;
         }
-        if (tid < 8) ctrl->peer_last[tid] = -1;
+        if (tid < kResMaxCluster) ctrl->peer_last[tid] = -1;
         __syncthreads();
 
         const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
@@ -376,14 +377,14 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                    : item_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, comp, J.lam, mode, nlow);
                     }
                 };
-                // A scan round: each warp takes the bitmap words warp, warp + NW, ... of this parity
-                // (one per lane), consumes their bits and appends the groups it found to the block's
-                // queue.  After a block barrier the queue is split evenly over the warps, and each
-                // warp tests and lowers its share on its own: no other block barrier until the end
-                // of the phase (or of the round, when the bitmap needs several).
+                // A scan round: warp w takes the round's bitmap words 32 w .. 32 w + 31 of this parity
+                // (one per lane; a small bitmap keeps only the first warps scanning), consumes their bits
+                // and appends the groups it found to the block's queue.  After a block barrier the queue
+                // is split over the warps, and each warp tests and lowers its share on its own: no other
+                // block barrier until the end of the phase (or of the round, when the bitmap needs several).
                 for (int r0 = 0; r0 < slot_words; r0 += 32 * NW) {
                     {
-                        const int wi = r0 + lane * NW + warp;
+                        const int wi = r0 + warp * 32 + lane;  // 32 consecutive words a warp: few warps scan
                         uint32_t d = 0;
                         int cr = 0;
                         if (wi < slot_words) {
@@ -668,6 +669,9 @@ template <int NW, int ES>
 cudaError_t resident_shape(int C, int n, size_t smem, int *grid)
 {
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(k_resident<NW, ES>));
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_resident<NW, ES>),
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cudaLaunchAttribute attr[1];
@@ -719,14 +723,38 @@ cudaError_t resident_shape_for(int nw, int es, int C, int n, size_t smem, int *g
 
 }  // namespace
 
-// Smallest cluster (1, 2, 4, 8 blocks of nw warps) whose shared memory holds
-// the image; 0 if none.
+// Largest cluster the device can run with blocks of nw warps and smem_limit
+// bytes of shared memory each: 16 where clusters of 16 (a non-portable size)
+// can be resident, else 8.  Asked once per device.
+int resident_max_cluster(int nw, size_t smem_limit)
+{
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 8;
+    }
+    if (!cached[dev]) {
+        int g1 = 0, g2 = 0;
+        const cudaError_t e1 = resident_shape_for(nw, 1, kResMaxCluster, 1, smem_limit, &g1);
+        const cudaError_t e2 = resident_shape_for(nw, 2, kResMaxCluster, 1, smem_limit, &g2);
+        cudaGetLastError();
+        cached[dev] = (e1 == cudaSuccess && e2 == cudaSuccess && g1 == kResMaxCluster && g2 == kResMaxCluster)
+                          ? kResMaxCluster
+                          : 8;
+    }
+    return cached[dev];
+}
+
+// Smallest cluster (1, 2, 4, 8, or 16 where the device allows it, blocks of
+// nw warps) whose shared memory holds the image; 0 if none.
 int resident_cluster_size(int w, int h, int dtype, size_t smem_limit, int nw, int *rows_out, int *rp_out)
 {
     const int es = dtype == THIN_U16 ? 2 : 1;
     const int rp = int((size_t(w) * es + 15) / 16 * 16) + 32;
     const int cw = (w + 7) / 8, wpr = (cw + 31) / 32;
-    for (int C = 1; C <= 8; C *= 2) {
+    const int cmax = resident_max_cluster(nw, smem_limit);
+    for (int C = 1; C <= cmax; C *= 2) {
         int rows = (h + C - 1) / C;
         rows += rows & 1;
         const int held = rows + (C > 1 ? 2 * std::min(kResStep, rows) : 0);  // halo: see resident_run

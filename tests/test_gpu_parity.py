@@ -312,11 +312,14 @@ def test_48_batch_plan_and_full_size():
 # ---------------------------------------------------------------- wide resident mode
 
 @pytest.mark.parametrize("shape,dt,lam", [((1400, 1400), "u8", 0), ((1400, 1400), "u8", 3), ((1000, 1100), "u16", 0),
-                                          ((200, 12000), "u8", 2), ((1300, 1500), "u8", 0)])
+                                          ((200, 12000), "u8", 2), ((1300, 1500), "u8", 0), ((2100, 1900), "u8", 0),
+                                          ((1500, 1400), "u16", 0)])
 def test_wide_matches_oracle(shape, dt, lam):
-    """Images larger than one cluster's shared memory, held by several clusters
-    of one launch (boundary rows cross through global memory every 8 phases);
-    the default engine and the resident engine forced both take the wide mode."""
+    """Images larger than an 8-block cluster's shared memory: held by one
+    cluster of 16 where the device runs such clusters and the image fits one,
+    else by several clusters of one launch (the wide mode: boundary rows cross
+    through global memory every 8 phases).  The default engine and the
+    resident engine forced both keep the image on chip."""
     img = synth.value_noise_image(*shape, dt, seed=shape[0] + 3 * shape[1] + lam)
     ref, rst = oracle.thin(img, lam)
     for kernel in ("auto", "resident"):
