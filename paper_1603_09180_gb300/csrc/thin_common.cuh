@@ -146,31 +146,10 @@ constexpr PointTable make_point_table(int adj)
 constexpr PointTable kPointTable = make_point_table(0);
 constexpr PointTable kPointTable48 = make_point_table(1);
 
-// For each lower mask m: byte j holds the ring mask of the j-th counted T--
-// component (the 4-components of Gamma^-- that hold a 4-neighbour of x);
-// unused bytes are 0.  Used by the lambda rule of k-divergent points.
-constexpr PointTable make_component_table(int adj)
-{
-    PointTable t{};
-    for (unsigned m = 0; m < 256; ++m) {
-        const uint32_t e = adj ? point_entry48(m) : point_entry(m);
-        uint32_t v = 0;
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t lab = (e >> (kTabLabelShift + 3 * i)) & 7u;
-            if (lab) v |= (1u << i) << (8 * (lab - 1));
-        }
-        t.v[m] = v;
-    }
-    return t;
-}
-
-constexpr PointTable kComponentTable = make_component_table(0);
-constexpr PointTable kComponentTable48 = make_component_table(1);
-
-// Shared-memory table block of every kernel: point and component tables of
-// (8,4), then of (4,8), 256 words each.
-constexpr int kTabWords = 1024;
-constexpr int kTabOffset48 = 512;
+// Shared-memory table block of every kernel: the point table of (8,4), then
+// that of (4,8), 256 words each.
+constexpr int kTabWords = 512;
+constexpr int kTabOffset48 = 256;
 
 #ifdef __CUDACC__
 

@@ -67,12 +67,10 @@ constexpr bool kOkPass = true;
 constexpr bool kFix = true;
 
 __device__ const PointTable d_res_point_table = kPointTable;
-__device__ const PointTable d_res_component_table = kComponentTable;
 __device__ const PointTable d_res_point_table48 = kPointTable48;
-__device__ const PointTable d_res_component_table48 = kComponentTable48;
 
 // Shared-memory map of one block for a job.
-constexpr int kOffTabs = 0;      // point and component tables of (8,4) and (4,8), 4 KiB
+constexpr int kOffTabs = 0;      // point tables of (8,4) and (4,8), 2 KiB (the block up to 4 KiB is free)
 constexpr int kOffCtrl = 4096;   // control words
 constexpr int kOffBar = 4352;    // mbarrier of the row staging
 constexpr int kOffRows = 4480;   // image rows (16-byte aligned)
@@ -200,9 +198,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
 
     for (int i = tid; i < 256; i += blockDim.x) {
         tabs[i] = d_res_point_table.v[i];
-        tabs[256 + i] = d_res_component_table.v[i];
         tabs[kTabOffset48 + i] = d_res_point_table48.v[i];
-        tabs[kTabOffset48 + 256 + i] = d_res_component_table48.v[i];
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -294,7 +290,6 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
 
         const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
         const uint32_t Mcw = CW > 1 ? 0xffffffffu / uint32_t(CW) + 1u : 0u;
-        const uint32_t *comp = tabs + 256;
 
         long long g = P.start_phase;
         unsigned qround = 0;  // scan rounds so far: selects the queue counter
@@ -351,30 +346,30 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                 // the (8,4) point test on four points at once, in the common mode's own build where it applies
                 auto test_item = [&](const uint8_t *rb, int pxx, uint32_t vm) -> uint32_t {
                     if constexpr (ES == 1) {
-                        return (kFix && mode == 0) ? test_u8<0>(rb - RP, rb, rb + RP, pxx, vm, comp, J.lam, mode)
-                                                   : test_u8(rb - RP, rb, rb + RP, pxx, vm, comp, J.lam, mode);
+                        return (kFix && mode == 0) ? test_u8<0>(rb - RP, rb, rb + RP, pxx, vm, J.lam, mode)
+                                                   : test_u8(rb - RP, rb, rb + RP, pxx, vm, J.lam, mode);
                     } else {
                         const uint16_t *r16 = reinterpret_cast<const uint16_t *>(rb);
                         const int rp16 = RP / 2;
-                        return (kFix && mode == 0) ? test_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, comp, J.lam, mode)
-                                                   : test_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, comp, J.lam, mode);
+                        return (kFix && mode == 0) ? test_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, J.lam, mode)
+                                                   : test_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, J.lam, mode);
                     }
                 };
                 // the lowering loop on four points (ok: a first test's result, or ~0u to test first)
                 auto lower_item = [&](uint8_t *rb, int pxx, uint32_t vm, uint32_t in, uint32_t ok) -> uint32_t {
                     if constexpr (ES == 1) {
                         if (ok == ~0u)
-                            return (kFix && mode == 0) ? item_u8<0>(rb - RP, rb, rb + RP, pxx, vm, in, comp, J.lam, mode, nlow)
-                                                       : item_u8(rb - RP, rb, rb + RP, pxx, vm, in, comp, J.lam, mode, nlow);
+                            return (kFix && mode == 0) ? item_u8<0>(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow)
+                                                       : item_u8(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow);
                         return (kFix && mode == 0)
-                                   ? item_u8_tested<0>(rb - RP, rb, rb + RP, pxx, vm, in, ok, comp, J.lam, mode, nlow)
-                                   : item_u8_tested(rb - RP, rb, rb + RP, pxx, vm, in, ok, comp, J.lam, mode, nlow);
+                                   ? item_u8_tested<0>(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow)
+                                   : item_u8_tested(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow);
                     } else {
                         uint16_t *r16 = reinterpret_cast<uint16_t *>(rb);
                         const int rp16 = RP / 2;
                         return (kFix && mode == 0)
-                                   ? item_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, comp, J.lam, mode, nlow)
-                                   : item_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, comp, J.lam, mode, nlow);
+                                   ? item_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow)
+                                   : item_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow);
                     }
                 };
                 // A scan round: warp w takes the round's bitmap words 32 w .. 32 w + 31 of this parity

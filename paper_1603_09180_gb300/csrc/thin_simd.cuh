@@ -109,15 +109,13 @@ __device__ __forceinline__ uint32_t equal_mask4(uint32_t c, const uint32_t nb[8]
 // FIX >= 0 fixes the mode word at compile time (the kernels pass the common
 // mode, lambda-thinning with F^- = max, this way); FIX < 0 reads `mode`.
 template <int FIX = -1>
-__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                             uint32_t lam, int mode, uint32_t M);
+__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, uint32_t lam, int mode, uint32_t M);
 
 template <int FIX = -1>
-__device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                            uint32_t lam, int mode, uint32_t &M)
+__device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], uint32_t vm, uint32_t lam, int mode, uint32_t &M)
 {
     M = lower_mask4(c, nb);
-    return decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
+    return decide4m<FIX>(c, nb, vm, lam, mode, M);
 }
 
 // The decision of Sec. 2.1 from masks alone (bit d of byte k: direction d of
@@ -126,8 +124,7 @@ __device__ __forceinline__ uint32_t decide4(uint32_t c, const uint32_t nb[8], ui
 // or the skeleton's test needs it.  The test depends on the pixel values
 // through these two masks only.
 template <int FIX, typename Below>
-__device__ __forceinline__ uint32_t decide_masks(uint32_t M, uint32_t vm, const uint32_t *comp, uint32_t lam,
-                                                 int mode_rt, Below below)
+__device__ __forceinline__ uint32_t decide_masks(uint32_t M, uint32_t vm, uint32_t lam, int mode_rt, Below below)
 {
     const int mode = FIX >= 0 ? FIX : mode_rt;
     const int rule = mode & 1;
@@ -144,18 +141,17 @@ __device__ __forceinline__ uint32_t decide_masks(uint32_t M, uint32_t vm, const 
         D = below();
         haveD = true;
         const uint32_t deep = D & mc;
-        // F^- = max: a component fails when no member is shallow (value >= F(x) - lambda);
-        // F^- = min: a component fails when some member is deep
+        // The counted components are the cyclic runs of mc.  F^- = max: a component fails when no
+        // member is shallow (value >= F(x) - lambda); F^- = min: when some member is deep.  The
+        // probe bits are carried towards the start of their run (a run of a k-divergent point has
+        // at most 5 bits), so a run's start is reached exactly when the run holds a probe bit.
         const uint32_t probe = rule == 0 ? (mc & ~deep) : deep;
-        uint32_t okdv = 0;
+        uint32_t fill = probe;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t e = comp[(M >> (8 * k)) & 0xffu];  // component masks, one per byte
-            const uint32_t hit = __popc(nonzero8(e & (((probe >> (8 * k)) & 0xffu) * kLsb8)));
-            const uint32_t bad = rule == 0 ? __popc(nonzero8(e)) - hit : hit;
-            okdv |= (bad <= 1 ? 1u : 0u) << (8 * k);
-        }
-        ok |= okdv & dv;
+        for (int i = 0; i < 4; ++i) fill |= rot_next(fill) & mc;
+        const uint32_t bad = rule == 0 ? (st & ~fill) : (st & fill);  // failing components, by their start
+        const uint32_t two = nonzero8(bad & ((bad | kMsb8) - kLsb8));   // two or more of them
+        ok |= (~two >> 7) & dv;
     }
     if (mode & 2) {
         // shallow: some lower neighbour >= F(x) - lambda, i.e. F(x) - alpha^- <= lambda
@@ -171,10 +167,9 @@ __device__ __forceinline__ uint32_t decide_masks(uint32_t M, uint32_t vm, const 
 
 // decide4 with the lower masks M of the centre values c already computed.
 template <int FIX>
-__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, const uint32_t *comp,
-                                             uint32_t lam, int mode_rt, uint32_t M)
+__device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], uint32_t vm, uint32_t lam, int mode_rt, uint32_t M)
 {
-    return decide_masks<FIX>(M, vm, comp, lam, mode_rt, [&] {
+    return decide_masks<FIX>(M, vm, lam, mode_rt, [&] {
         const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
         const uint32_t cl = __vsubus4(c, lrep);
         const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
@@ -188,17 +183,16 @@ __device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], u
 // The lowering loop of Sec. 2.2 on the four points: while a point is
 // lambda-destructible, F(x) := alpha^-(x, F), its neighbours fixed.  Returns
 // the bytes lowered (0x01 each) over all iterations; `c` receives the new
-// values, `nin` the lowering steps of the points also in `in`.  `comp` is the
-// component-mask table.
+// values, `nin` the lowering steps of the points also in `in`.
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
-                                           const uint32_t *comp, uint32_t lam, int mode, int &nin)
+                                           uint32_t lam, int mode, int &nin)
 {
     uint32_t okacc = 0;
     uint32_t M = lower_mask4(c, nb);
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
-        const uint32_t ok = decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
+        const uint32_t ok = decide4m<FIX>(c, nb, vm, lam, mode, M);
         if (!ok) break;
         const uint32_t alpha = alpha4(nb, M);
         const uint32_t okm = ok * 0xffu;
@@ -214,7 +208,7 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
 // (0x01 per byte that may be lowered at the current values).
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
-                                                  uint32_t ok, const uint32_t *comp, uint32_t lam, int mode, int &nin)
+                                                  uint32_t ok, uint32_t lam, int mode, int &nin)
 {
     uint32_t okacc = 0;
     uint32_t M = lower_mask4(c, nb);
@@ -227,7 +221,7 @@ __device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb
         okacc |= ok;
         nin += __popc(ok & in);
         M &= ~equal_mask4(c, nb);
-        ok = decide4m<FIX>(c, nb, vm, comp, lam, mode, M);
+        ok = decide4m<FIX>(c, nb, vm, lam, mode, M);
     }
     return okacc;
 }
@@ -279,21 +273,21 @@ __device__ __forceinline__ void gather_u8(const uint8_t *ra, const uint8_t *rb, 
 // One u8 work item, tested only: 0x01 in the bytes of the points that would be lowered now.
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t test_u8(const uint8_t *ra, const uint8_t *rb, const uint8_t *rc, int px,
-                                            uint32_t vm, const uint32_t *comp, uint32_t lam, int mode)
+                                            uint32_t vm, uint32_t lam, int mode)
 {
     uint32_t nb[8], c, other, M;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    return decide4<FIX>(c, nb, vm, comp, lam, mode, M);
+    return decide4<FIX>(c, nb, vm, lam, mode, M);
 }
 
 // One u8 work item, lowered: the lowering loop on its four points, the block written back.
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
-                                            uint32_t in, const uint32_t *comp, uint32_t lam, int mode, int &nin)
+                                            uint32_t in, uint32_t lam, int mode, int &nin)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4<FIX>(c, nb, vm, in, comp, lam, mode, nin);
+    const uint32_t moved = lower4<FIX>(c, nb, vm, in, lam, mode, nin);
     if (moved) {
         uint2 out;
         if (px == 0)
@@ -308,12 +302,11 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
 // item_u8 for a work item whose first test already ran (result `ok`).
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t item_u8_tested(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px,
-                                                   uint32_t vm, uint32_t in, uint32_t ok, const uint32_t *comp,
-                                                   uint32_t lam, int mode, int &nin)
+                                                   uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4_tested<FIX>(c, nb, vm, in, ok, comp, lam, mode, nin);
+    const uint32_t moved = lower4_tested<FIX>(c, nb, vm, in, ok, lam, mode, nin);
     if (moved) {
         uint2 out;
         if (px == 0)
@@ -421,10 +414,10 @@ __device__ __forceinline__ void alpha16(const Px16 &P, uint32_t M, uint32_t &aA,
 }
 
 template <int FIX>
-__device__ __forceinline__ uint32_t decide16m(const Px16 &P, uint32_t vm, const uint32_t *comp, uint32_t lam, int mode,
+__device__ __forceinline__ uint32_t decide16m(const Px16 &P, uint32_t vm, uint32_t lam, int mode,
                                               uint32_t M)
 {
-    return decide_masks<FIX>(M, vm, comp, lam, mode, [&] {
+    return decide_masks<FIX>(M, vm, lam, mode, [&] {
         const uint32_t lrep = (lam > 65535u ? 65535u : lam) * 0x00010001u;
         return lower_mask16(P, __vsubus2(P.cA, lrep), __vsubus2(P.cB, lrep));
     });
@@ -434,12 +427,11 @@ __device__ __forceinline__ uint32_t decide16m(const Px16 &P, uint32_t vm, const 
 // already made at the current values, or ~0u to test first.  Returns the bytes
 // lowered (0x01 each); P.cA, P.cB receive the new values.
 template <int FIX>
-__device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, uint32_t ok, const uint32_t *comp,
-                                            uint32_t lam, int mode, int &nin)
+__device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin)
 {
     uint32_t okacc = 0;
     uint32_t M = lower_mask16(P, P.cA, P.cB);
-    if (ok == ~0u) ok = decide16m<FIX>(P, vm, comp, lam, mode, M);
+    if (ok == ~0u) ok = decide16m<FIX>(P, vm, lam, mode, M);
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
         if (!ok) break;
@@ -451,7 +443,7 @@ __device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, u
         okacc |= ok;
         nin += __popc(ok & in);
         M &= ~equal_mask16(P);  // unmoved points: no neighbour equal to c is lower
-        ok = decide16m<FIX>(P, vm, comp, lam, mode, M);
+        ok = decide16m<FIX>(P, vm, lam, mode, M);
     }
     return okacc;
 }
@@ -523,25 +515,25 @@ __device__ __forceinline__ void store_u16(uint16_t *rb, int px, const Px16 &P, u
 // One u16 work item under (8,4), tested only: 0x01 in the bytes of the points that would be lowered now.
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t test_u16(const uint16_t *ra, const uint16_t *rb, const uint16_t *rc, int px,
-                                             uint32_t vm, const uint32_t *comp, uint32_t lam, int mode)
+                                             uint32_t vm, uint32_t lam, int mode)
 {
     Px16 P;
     uint4 w;
     gather_u16(ra, rb, rc, px, P, w);
-    return decide16m<FIX>(P, vm, comp, lam, mode, lower_mask16(P, P.cA, P.cB));
+    return decide16m<FIX>(P, vm, lam, mode, lower_mask16(P, P.cA, P.cB));
 }
 
 // One u16 work item under (8,4), lowered (ok: a first test's result, or ~0u);
 // the block is written back if a point moved.
 template <int FIX = -1>
 __device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px, uint32_t vm,
-                                             uint32_t in, uint32_t ok, const uint32_t *comp, uint32_t lam, int mode,
+                                             uint32_t in, uint32_t ok, uint32_t lam, int mode,
                                              int &nin)
 {
     Px16 P;
     uint4 w;
     gather_u16(ra, rb, rc, px, P, w);
-    const uint32_t moved = lower16<FIX>(P, vm, in, ok, comp, lam, mode, nin);
+    const uint32_t moved = lower16<FIX>(P, vm, in, ok, lam, mode, nin);
     if (moved) store_u16(rb, px, P, w);
     return moved;
 }

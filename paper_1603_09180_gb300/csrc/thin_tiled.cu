@@ -109,9 +109,7 @@ struct EngineArgs {
 };
 
 __device__ const PointTable d_point_table = kPointTable;
-__device__ const PointTable d_component_table = kComponentTable;
 __device__ const PointTable d_point_table48 = kPointTable48;
-__device__ const PointTable d_component_table48 = kComponentTable48;
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -309,11 +307,11 @@ __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_
             T *rb = tile + sr * bw + sb;
             if (sizeof(T) == 1 && !(V.rule & 4))  // u8 under (8,4): four points at once
                 moved = item_u8(reinterpret_cast<const uint8_t *>(rb - bw), reinterpret_cast<uint8_t *>(rb),
-                                reinterpret_cast<const uint8_t *>(rb + bw), px, vm, in, tabs + 256, V.lam, V.rule,
+                                reinterpret_cast<const uint8_t *>(rb + bw), px, vm, in, V.lam, V.rule,
                                 nlow);
             else if (sizeof(T) == 2 && !(V.rule & 4))  // u16 under (8,4): four points in 16-bit lanes
                 moved = item_u16(reinterpret_cast<const uint16_t *>(rb - bw), reinterpret_cast<uint16_t *>(rb),
-                                 reinterpret_cast<const uint16_t *>(rb + bw), px, vm, in, ~0u, tabs + 256, V.lam,
+                                 reinterpret_cast<const uint16_t *>(rb + bw), px, vm, in, ~0u, V.lam,
                                  V.rule, nlow);
             else
                 moved = item_table<T>(rb - bw, rb, rb + bw, px, vm, in, tabs + ((V.rule & 4) ? kTabOffset48 : 0), V.lam,
@@ -364,7 +362,7 @@ __device__ __forceinline__ void decode(const EngineArgs &P, bool full, const uns
     tx = local - ty * D.tiles_x;
 }
 
-constexpr int kSmemTabs = 4 * kTabWords;  // point and component tables of (8,4) and (4,8), 256 x u32 each
+constexpr int kSmemTabs = 4 * kTabWords;  // point tables of (8,4) and (4,8), 256 x u32 each
 
 __global__ void __launch_bounds__(kThreads, 2) k_engine(EngineArgs P)
 {
@@ -383,9 +381,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_engine(EngineArgs P)
 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         tabs[i] = d_point_table.v[i];
-        tabs[256 + i] = d_component_table.v[i];
         tabs[kTabOffset48 + i] = d_point_table48.v[i];
-        tabs[kTabOffset48 + 256 + i] = d_component_table48.v[i];
     }
     if (lane == 0) {
         mbar_init(bar, 1);
