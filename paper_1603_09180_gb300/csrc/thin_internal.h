@@ -66,6 +66,15 @@ struct ResJob {
     int steph;  // phases between exchanges of halo rows
     int adj;    // thin_adj
     int done_slot;  // completion record of the job (ResArgs::done), -1 none
+    unsigned long long ck;  // first word of the job's checkpoint of its dirty bitmaps (ResArgs::ckbits)
+};
+
+// Where a job paused at the end of its last time slice (ResArgs::slice).
+struct ResRun {
+    long long g;     // global phase index to resume at
+    long long last;  // last phase that lowered a point, -1 if none
+    int resumed;     // 1: the job has a checkpoint to resume from
+    int pad;
 };
 
 struct ResStat {
@@ -87,7 +96,7 @@ struct ResDone {
 };
 
 struct ResCtl {
-    unsigned next_job;
+    unsigned head, tail;  // job ring: entries head .. tail - 1 wait to run (ResArgs::ring)
     int error;
     unsigned bar_count;  // grid barrier of a wide launch
     unsigned bar_gen;
@@ -110,6 +119,16 @@ struct ResArgs {
     unsigned char *xbuf;        // per block: 2 sides x 2 step parities x xslot bytes
     unsigned long long xslot;
     ResDone *done;              // completion records (ResJob::done_slot), nullptr: none
+    // Job ring and time slices.  Clusters take jobs from the ring in order.  With
+    // slice > 0, a cluster whose job has run `slice` more steps while other jobs
+    // wait stores the job's state (its rows to the image, its dirty bitmaps to
+    // ckbits, its phase to run[]) and puts it back at the ring's tail.
+    int *ring;                  // cap entries: job indices
+    unsigned *tag;              // per entry: 1 + the round of the ring it was written in
+    ResRun *run;                // per job
+    uint32_t *ckbits;           // checkpointed dirty bitmaps
+    unsigned cap;
+    int slice;                  // steps per time slice (a power of two), 0: jobs run to the end once started
 };
 
 // A resident launch prepared on the host (device tables uploaded), ready to
@@ -120,8 +139,8 @@ struct ResidentPrepared {
     size_t smem = 0;
     bool async_alloc = true;
     char *base = nullptr;         // one device allocation holding everything below
-    void *st0 = nullptr, *ctl0 = nullptr;  // pristine stats and control words
-    size_t st_bytes = 0;
+    char *live = nullptr, *pristine = nullptr;  // per-run state (stats, control, job ring) and its initial copy
+    size_t live_bytes = 0;
     std::vector<int> order;       // launch position -> index in the prepared job list
     ResArgs P;                    // the kernel's argument block
 };

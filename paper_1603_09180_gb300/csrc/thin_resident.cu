@@ -75,6 +75,10 @@ constexpr int kOffCtrl = 4096;   // control words
 constexpr int kOffBar = 4352;    // mbarrier of the row staging
 constexpr int kOffRows = 4480;   // image rows (16-byte aligned)
 constexpr int kResMaxCluster = 16;  // largest cluster (16 is a non-portable size, used where the device allows)
+// Steps (exchanges of halo rows) a job runs before it yields its cluster to a
+// waiting job, when a launch has more jobs than clusters: 1024 phases of
+// 8-row steps, about 4 ms of a 512^2 job.  A power of two.
+constexpr int kResSlice = 128;
 
 struct Ctrl {
     int job;
@@ -85,6 +89,7 @@ struct Ctrl {
     int bar_ok;              // result of the last grid barrier (wide launches)
     unsigned qn[2];          // fill counters of the block's group queue, alternating by scan round
     unsigned fail[2];        // wide launches, cluster leader: a block's grid-barrier wait failed (by step parity)
+    int yield;               // cluster leader: the job pauses at this time slice's end
 };
 static_assert(sizeof(Ctrl) <= kOffBar - kOffCtrl, "control words overlap the mbarrier");
 
@@ -174,6 +179,47 @@ __device__ bool res_grid_barrier(ResCtl *ctl, unsigned nblocks, unsigned long lo
     return *s_ok != 0;
 }
 
+// The job ring.  Entry t holds a job once tag[t % cap] == 1 + t / cap.  A pop
+// takes the head entry only while head < tail (an empty ring consumes
+// nothing, so a cluster that finds it empty may leave); a push appends at the
+// tail.  A cluster pushes only a job it paused while others waited, and pops
+// again at once, so every pushed job has a taker.  Returns the job, or -1 when
+// the ring is empty (or a bounded wait ran out: THIN_ERR_TIMEOUT posted).
+__device__ int res_pop(const ResArgs &P)
+{
+    volatile unsigned *head = &P.ctl->head, *tail = &P.ctl->tail;
+    const unsigned long long t0 = res_gtimer();
+    for (;;) {
+        const unsigned h = *head;
+        if (h >= *tail) return -1;
+        if (atomicCAS(&P.ctl->head, h, h + 1) != h) {  // another cluster took it: try the next one
+            if (res_gtimer() - t0 > P.timeout_ns) {
+                atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
+                return -1;
+            }
+            continue;
+        }
+        const unsigned s = h % P.cap, want = 1u + h / P.cap;
+        while (*reinterpret_cast<volatile unsigned *>(&P.tag[s]) != want) {  // its pusher is writing it
+            if (res_gtimer() - t0 > P.timeout_ns) {
+                atomicCAS(&P.ctl->error, 0, THIN_ERR_TIMEOUT);
+                return -1;
+            }
+        }
+        __threadfence();
+        return *reinterpret_cast<volatile int *>(&P.ring[s]);
+    }
+}
+
+__device__ void res_push(const ResArgs &P, int job)
+{
+    const unsigned t = atomicAdd(&P.ctl->tail, 1u);
+    const unsigned s = t % P.cap;
+    *reinterpret_cast<volatile int *>(&P.ring[s]) = job;
+    __threadfence();
+    *reinterpret_cast<volatile unsigned *>(&P.tag[s]) = 1u + t / P.cap;
+}
+
 // OR of m into bits[key] (key < 0: nothing to mark).  Combining the lanes
 // that name the same word first (__match_any_sync + __reduce_or_sync) was
 // measured slower than letting the shared-memory atomics serialise.
@@ -218,11 +264,11 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             if (iter > 0) break;  // a wide launch runs its one image
             job = 0;
         } else {
-            if (rank == 0 && tid == 0) ctrl->job = int(atomicAdd(&P.ctl->next_job, 1u));
+            if (rank == 0 && tid == 0) ctrl->job = res_pop(P);
             cluster.sync();
             job = cluster.map_shared_rank(ctrl, 0)->job;
             cluster.sync();  // every block has read the leader's word before it may leave or overwrite it
-            if (job >= P.njobs) break;
+            if (job < 0) break;
         }
         const ResJob J = P.jobs[job];
         constexpr int es = ES;
@@ -246,7 +292,9 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         const int rowb = J.w * es;
         const char *gimg = reinterpret_cast<const char *>(J.img);
 
-        // ---- stage own and halo rows that exist in the image
+        // ---- stage own and halo rows that exist in the image (with slices on, they may have been
+        // written by the cluster that paused the job: order them before this block's bulk copies)
+        if (P.slice > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         const int ya = max(0, ybase), yb = min(J.h, ybase + LR);
         const int nload = max(0, yb - ya);
         if (J.bulk && nload > 0) {
@@ -271,13 +319,28 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         } else {
             for (int e = tid; e < nload * rowb; e += blockDim.x) {
                 const int r = e / rowb, c = e - r * rowb;
-                rows_base[size_t(ya - ybase + r) * RP + 16 + c] = uint8_t(gimg[size_t(ya + r) * J.pitch + c]);
+                rows_base[size_t(ya - ybase + r) * RP + 16 + c] = uint8_t(__ldcg(gimg + size_t(ya + r) * J.pitch + c));
             }
         }
-        // every group is tested in the first phase of its parity
-        for (int i = tid; i < 4 * slot_words; i += blockDim.x) dirty[i] = 0xffffffffu;
+        // a fresh job tests every group in the first phase of its parity; a resumed one restores the
+        // dirty bitmaps of its checkpoint (written by another SM: read through L2)
+        ResRun run;
+        run.resumed = 0;
+        if (P.slice > 0) {
+            const volatile ResRun &vr = P.run[job];
+            run.g = vr.g;
+            run.last = vr.last;
+            run.resumed = vr.resumed;
+        }
+        if (run.resumed) {
+            const uint32_t *ck = P.ckbits + J.ck + size_t(rank) * 4 * slot_words;
+            for (int i = tid; i < 4 * slot_words; i += blockDim.x) dirty[i] = __ldcg(ck + i);
+        } else {
+            for (int i = tid; i < 4 * slot_words; i += blockDim.x) dirty[i] = 0xffffffffu;
+        }
+        const long long last0 = run.resumed ? run.last : -1;
         if (tid == 0) {
-            ctrl->last = -1;
+            ctrl->last = last0;
             ctrl->nlow = 0;
             ctrl->ntest = 0;
             ctrl->qn[0] = 0u;
@@ -285,16 +348,20 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             ctrl->fail[0] = 0u;
             ctrl->fail[1] = 0u;
         }
-        if (tid < kResMaxCluster) ctrl->peer_last[tid] = -1;
-        __syncthreads();
+        if (tid < kResMaxCluster) ctrl->peer_last[tid] = last0;
+        // No block may push its last change into a peer (end of the first step) before that peer has
+        // set its array above: the arrays must agree, or the blocks could take different stop
+        // decisions and their cluster barriers stop pairing.
+        cluster.sync();
 
         const uint32_t Mwpr = WPR > 1 ? 0xffffffffu / uint32_t(WPR) + 1u : 0u;
         const uint32_t Mcw = CW > 1 ? 0xffffffffu / uint32_t(CW) + 1u : 0u;
 
-        long long g = P.start_phase;
+        long long g = run.resumed ? run.g : P.start_phase;
         unsigned qround = 0;  // scan rounds so far: selects the queue counter
-        long long steps = 0;
+        unsigned steps = 0;   // steps of this job on this cluster
         int converged = 0;
+        bool paused = false;
         int nlow = 0, ntest = 0;
         for (;;) {  // steps of H phases between exchanges of halo rows
             const long long done = g - P.start_phase;
@@ -598,6 +665,18 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                 if (C > 1) cluster.sync();  // nobody changes its own rows before its neighbours have copied them
                 else __syncthreads();
             }
+            // end of a time slice: pause the job if other jobs wait for a cluster (the leader decides for
+            // the whole cluster; its word is next written a slice later, after many cluster barriers)
+            if (P.slice > 0 && (steps & unsigned(P.slice - 1)) == 0u) {
+                if (rank == 0 && tid == 0)
+                    ctrl->yield = *reinterpret_cast<volatile unsigned *>(&P.ctl->head) <
+                                  *reinterpret_cast<volatile unsigned *>(&P.ctl->tail);
+                cluster.sync();
+                if (cluster.map_shared_rank(ctrl, 0)->yield) {
+                    paused = true;
+                    break;
+                }
+            }
         }
         // ---- results
         nlow = __reduce_add_sync(0xffffffffu, nlow);
@@ -605,22 +684,50 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
         if (lane == 0 && nlow) atomicAdd(&ctrl->nlow, (unsigned long long)nlow);
         if (lane == 0 && ntest) atomicAdd(&ctrl->ntest, (unsigned long long)ntest);
         __syncthreads();
+        // the job's fields used from here on are read again (fewer registers live through the steps)
+        const ResJob &Jg = P.jobs[job];
         {
             const int ra = max(row0, 1), rb = min(row0 + R, J.h - 1);  // border rows never change
-            char *gout = reinterpret_cast<char *>(J.img);
-            if (J.bulk) {
+            char *gout = reinterpret_cast<char *>(Jg.img);
+            const unsigned long long pitch = Jg.pitch;
+            if (Jg.bulk) {
                 const int vpr = rowb / 16;
                 for (int e = tid; e < max(0, rb - ra) * vpr; e += blockDim.x) {
                     const int r = e / vpr, c = e - r * vpr;
-                    *reinterpret_cast<uint4 *>(gout + size_t(ra + r) * J.pitch + 16 * c) =
+                    *reinterpret_cast<uint4 *>(gout + size_t(ra + r) * pitch + 16 * c) =
                         *reinterpret_cast<const uint4 *>(rows_base + size_t(ra + r - ybase) * RP + 16 + 16 * c);
                 }
             } else {
                 for (int e = tid; e < max(0, rb - ra) * rowb; e += blockDim.x) {
                     const int r = e / rowb, c = e - r * rowb;
-                    gout[size_t(ra + r) * J.pitch + c] = char(rows_base[size_t(ra + r - ybase) * RP + 16 + c]);
+                    gout[size_t(ra + r) * pitch + c] = char(rows_base[size_t(ra + r - ybase) * RP + 16 + c]);
                 }
             }
+        }
+        if (paused) {
+            // checkpoint: the rows went to the image above; the dirty bitmaps, the counts and the
+            // phase to resume at go to global memory, then the job goes back to the ring's tail
+            uint32_t *ckw = P.ckbits + Jg.ck + size_t(rank) * 4 * slot_words;
+            for (int i = tid; i < 4 * slot_words; i += blockDim.x) __stcg(ckw + i, dirty[i]);
+            if (tid == 0) {
+                ResStat &St = P.st[job];
+                atomicAdd(&St.lowered, ctrl->nlow);
+                atomicAdd(&St.tested, ctrl->ntest);
+                if (rank == 0) {
+                    long long lc = -1;
+                    for (int q = 0; q < C; ++q) lc = max(lc, ctrl->peer_last[q]);
+                    volatile ResRun &vr = P.run[job];
+                    vr.g = g;
+                    vr.last = lc;
+                    vr.resumed = 1;
+                }
+            }
+            __threadfence();
+            asm volatile("fence.proxy.async.global;" ::: "memory");       // the rows are read back by bulk copies
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the next bulk copy
+            cluster.sync();  // every block's rows and bitmaps are out
+            if (rank == 0 && tid == 0) res_push(P, job);
+            continue;
         }
         if (tid == 0) {
             ResStat &St = P.st[job];
@@ -637,14 +744,15 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes before the next bulk copy
-        const bool post = P.done != nullptr && J.done_slot >= 0;
+        const int done_slot = Jg.done_slot;
+        const bool post = P.done != nullptr && done_slot >= 0;
         if (post) __threadfence_system();  // this block's rows are out before the leader posts the record
         cluster.sync();  // nobody reads this job's rows or control words any more
         if (post && rank == 0 && tid == 0) {
             // completion record: the job's stats (every block added its counts before the cluster barrier),
             // then the flag, released at system scope for the host that polls it
             const volatile ResStat &S = P.st[job];
-            ResDone *d = P.done + J.done_slot;
+            ResDone *d = P.done + done_slot;
             d->st.lowered = S.lowered;
             d->st.tested = S.tested;
             d->st.last_change = S.last_change;
@@ -875,47 +983,80 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     R->order = order;
     R->smem = smem;
 
+    // launch shape first: time slices only pay when more jobs than clusters wait
+    const int want = strips > 0 ? strips : n;  // clusters wanted
+    cudaError_t e = resident_shape_for(nw, R->es, C, want, smem, &R->grid);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (strips > 0 && R->grid < B) return THIN_ERR_ARG;  // not all strips fit at once
+    const int clusters = std::max(1, R->grid / C);
+    const int slice = (strips == 0 && n > clusters) ? kResSlice : 0;
+    const unsigned cap = unsigned(n + clusters);  // ring entries: queued jobs plus one pop in flight per cluster
+    size_t ck_words = 0;
+    if (slice > 0)
+        for (auto &r : sorted) {
+            r.ck = ck_words;
+            ck_words += size_t(C) * 4 * ((r.rows + 2 * r.hr) / 2) * r.wpr;
+        }
+
+    // one allocation: job table | live state (stats, control, per-job run, ring tags, ring) | its
+    // pristine copy, the same layout | checkpoints | wide-mode exchange slots
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     const size_t o_jobs = 0;
-    const size_t st_bytes = (sizeof(ResStat) * n + 255) / 256 * 256;
-    const size_t o_st = (sizeof(ResJob) * n + 255) / 256 * 256;
-    const size_t o_ctl = o_st + st_bytes;
-    const size_t o_st0 = o_ctl + 256;
-    const size_t o_ctl0 = o_st0 + st_bytes;
+    const size_t l_st = 0, l_ctl = up(sizeof(ResStat) * n), l_run = l_ctl + up(sizeof(ResCtl));
+    const size_t l_tag = l_run + up(sizeof(ResRun) * n), l_ring = l_tag + up(sizeof(unsigned) * cap);
+    const size_t live_bytes = l_ring + up(sizeof(int) * cap);
+    const size_t o_live = up(sizeof(ResJob) * n);
+    const size_t o_prist = o_live + live_bytes;
+    const size_t o_ck = o_prist + live_bytes;
     // wide: per block, 2 sides x 2 step parities of (halo rows + their dirty words)
     size_t xslot = 0;
     if (strips > 0) {
         const ResJob &r = rj[0];
-        xslot = (size_t(r.hr) * r.rp + size_t(4) * (r.hr / 2 + 1) * r.wpr * 4 + 255) / 256 * 256;
+        xslot = up(size_t(r.hr) * r.rp + size_t(4) * (r.hr / 2 + 1) * r.wpr * 4);
     }
-    const size_t o_x = o_ctl0 + 256;
+    const size_t o_x = o_ck + up(ck_words * 4);
     const size_t total = o_x + xslot * 4 * size_t(B);
-    cudaError_t e = async_alloc ? cudaMallocAsync(reinterpret_cast<void **>(&R->base), total, stream)
-                                : cudaMalloc(reinterpret_cast<void **>(&R->base), total);
+    e = async_alloc ? cudaMallocAsync(reinterpret_cast<void **>(&R->base), total, stream)
+                    : cudaMalloc(reinterpret_cast<void **>(&R->base), total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         R->base = nullptr;
         return THIN_ERR_OOM;
     }
-    std::vector<ResStat> st0(n);
-    for (auto &x : st0) {
-        std::memset(&x, 0, sizeof x);
-        x.last_change = -1;
+    // the pristine live state: fresh stats, every job queued in order
+    std::vector<char> prist(live_bytes, 0);
+    ResStat *st0 = reinterpret_cast<ResStat *>(prist.data() + l_st);
+    for (int k = 0; k < n; ++k) st0[k].last_change = -1;
+    ResCtl *ctl0 = reinterpret_cast<ResCtl *>(prist.data() + l_ctl);
+    ctl0->gl_last = -1;
+    ctl0->head = 0;
+    ctl0->tail = unsigned(n);
+    ResRun *run0 = reinterpret_cast<ResRun *>(prist.data() + l_run);
+    for (int k = 0; k < n; ++k) run0[k].last = -1;
+    unsigned *tag0 = reinterpret_cast<unsigned *>(prist.data() + l_tag);
+    int *ring0 = reinterpret_cast<int *>(prist.data() + l_ring);
+    for (int k = 0; k < n; ++k) {
+        ring0[k] = k;
+        tag0[k] = 1u;  // written in round 0
     }
-    ResCtl ctl0;
-    std::memset(&ctl0, 0, sizeof ctl0);
-    ctl0.gl_last = -1;
     e = cudaMemcpyAsync(R->base + o_jobs, sorted.data(), sizeof(ResJob) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_st0, st0.data(), sizeof(ResStat) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_ctl0, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, stream);
-    R->st0 = R->base + o_st0;
-    R->ctl0 = R->base + o_ctl0;
-    R->st_bytes = sizeof(ResStat) * n;
+    // (pageable sources: each copy has taken its bytes when it returns)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R->base + o_prist, prist.data(), live_bytes, cudaMemcpyHostToDevice, stream);
+    R->live = R->base + o_live;
+    R->pristine = R->base + o_prist;
+    R->live_bytes = live_bytes;
 
     ResArgs &P = R->P;
     std::memset(&P, 0, sizeof P);
     P.jobs = reinterpret_cast<const ResJob *>(R->base + o_jobs);
-    P.st = reinterpret_cast<ResStat *>(R->base + o_st);
-    P.ctl = reinterpret_cast<ResCtl *>(R->base + o_ctl);
+    P.st = reinterpret_cast<ResStat *>(R->live + l_st);
+    P.ctl = reinterpret_cast<ResCtl *>(R->live + l_ctl);
+    P.run = reinterpret_cast<ResRun *>(R->live + l_run);
+    P.tag = reinterpret_cast<unsigned *>(R->live + l_tag);
+    P.ring = reinterpret_cast<int *>(R->live + l_ring);
+    P.ckbits = slice > 0 ? reinterpret_cast<uint32_t *>(R->base + o_ck) : nullptr;
+    P.cap = cap;
+    P.slice = slice;
     P.njobs = n;
     P.rule = test_mode(opt);  // F^- reading and operator
     P.start_phase = opt.start_phase;
@@ -926,11 +1067,6 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
     P.xslot = xslot;
     P.done = strips > 0 ? nullptr : done;
     if (const char *t = std::getenv("THIN_TIMEOUT_NS")) P.timeout_ns = std::strtoull(t, nullptr, 10);
-    if (e == cudaSuccess) {
-        const int want = strips > 0 ? strips : n;  // clusters wanted
-        e = resident_shape_for(nw, R->es, C, want, smem, &R->grid);
-        if (e == cudaSuccess && strips > 0 && R->grid < B) return THIN_ERR_ARG;  // not all strips fit at once
-    }
     return e == cudaSuccess ? THIN_OK : cuda_status(e);
 }
 
@@ -938,8 +1074,7 @@ int resident_prepare(const JobSpec *jobs, int n, int C, int nw, const thin_optio
 // launches: device work only, so it can be captured in a CUDA graph.
 cudaError_t resident_enqueue(const ResidentPrepared &R, cudaStream_t stream)
 {
-    cudaError_t e = cudaMemcpyAsync(R.P.st, R.st0, R.st_bytes, cudaMemcpyDeviceToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(R.P.ctl, R.ctl0, sizeof(ResCtl), cudaMemcpyDeviceToDevice, stream);
+    const cudaError_t e = cudaMemcpyAsync(R.live, R.pristine, R.live_bytes, cudaMemcpyDeviceToDevice, stream);
     if (e != cudaSuccess) return e;
     return R.es == 2 ? resident_launch<kResMaxWarps, 2>(R.C, R.grid, R.smem, stream, R.P)
                      : resident_launch<kResMaxWarps, 1>(R.C, R.grid, R.smem, stream, R.P);

@@ -113,17 +113,21 @@ def test_serve_small_images_do_not_wait_for_a_slow_one():
     with thin.Server(1 << 30, max_slots=8 * 64, queue_cap=64) as srv:
         ts = srv.submit(slow, 20)
         tk = [srv.submit(im, 0) for im in small]
-        order = []
+        order, outs = [], {}
         while len(order) < 1 + len(small):
             t = srv.wait_any(20000)
             assert t is not None
             done, out, st, rc = srv.poll(t)
             assert done and rc == 0
             order.append(t)
-            img, lam = (slow, 20) if t == ts else (small[tk.index(t)], 0)
-            ref, _ = alone(img, lam)
-            assert np.array_equal(out, ref)
+            outs[t] = out
+    # the results are checked after the server is gone: a synchronising call from this thread while
+    # the slow image runs could hold up the lanes' launches and change the order being tested
     assert order[-1] == ts
+    for t, out in outs.items():
+        img, lam = (slow, 20) if t == ts else (small[tk.index(t)], 0)
+        ref, _ = alone(img, lam)
+        assert np.array_equal(out, ref)
 
 
 def test_serve_queue_cap_and_budget():
