@@ -65,6 +65,15 @@ constexpr int kResStep = 8;  // phases between halo exchanges = halo rows held f
 constexpr int kTwoPass = 32;
 constexpr bool kOkPass = true;
 constexpr bool kFix = true;
+// Which neighbours of a lowered point become dirty (marks8 / marks16): 0 all
+// eight; 1 those above the point's new value; 2 those also at most its old
+// value + lambda (the second bound only outside the wide mode, where it was
+// measured to cost more than it saves).  The skipped ones cannot change their
+// test result.
+#ifndef THIN_RES_MARK
+#define THIN_RES_MARK 2
+#endif
+constexpr int kMark = THIN_RES_MARK;
 
 __device__ const PointTable d_res_point_table = kPointTable;
 __device__ const PointTable d_res_point_table48 = kPointTable48;
@@ -373,28 +382,40 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                 // rows whose points are exact in this phase: own rows and Hs-1-j halo rows
                 const int rr = B > 1 ? Hs - 1 - j : 0;
                 const int ylo = max(1, row0 - rr), yhi = min(J.h - 2, row0 + R - 1 + rr);
-                // the groups of the other three parities next to a moved point become dirty
-                // (moved == 0: nothing to mark)
+                // the groups of the other three parities holding a neighbour to test again become
+                // dirty.  A: byte k holds the ring directions (bit 0 E, 1 NE, 2 N, 3 NW, 4 W, 5 SW,
+                // 6 S, 7 SE) of point k's neighbours to mark; 0: nothing to mark.  E and W neighbours
+                // are in the row's other column parity, N and S in the other row parity, the
+                // diagonals in the fourth.  For px == 0 the W side of point 0 is in the cell to the
+                // left; for px == 1 the E side of point 3 is in the cell to the right.
                 const int qrow = 2 * py + (px ^ 1), qcol = 2 * (py ^ 1) + px, qdiag = 2 * (py ^ 1) + (px ^ 1);
-                auto mark = [&](int cr, int cc, uint32_t moved) {
-                    const bool lo = px == 0 && (moved & 1u);           // x - 1 of point 0 is left of the block
-                    const bool hi = px == 1 && (moved & 0x01000000u);  // x + 1 of point 3 is right of it
+                auto mark = [&](int cr, int cc, uint32_t A) {
+                    const uint32_t rs = A & (px ? 0x10111111u : 0x11111101u);  // same cell: E, W
+                    const uint32_t as = A & (px ? 0x080a0a0au : 0x0a0a0a02u);  // NE, NW
+                    const uint32_t bs = A & (px ? 0x20a0a0a0u : 0xa0a0a080u);  // SE, SW
+                    const uint32_t rx = A & (px ? 0x01000000u : 0x00000010u);  // the cell beside
+                    const uint32_t ax = A & (px ? 0x02000000u : 0x00000008u);
+                    const uint32_t bx = A & (px ? 0x80000000u : 0x00000020u);
                     const int w = cc >> 5, b = cc & 31;
                     const uint32_t mc = 1u << b;
-                    const uint32_t mlr = mc | (lo && b > 0 ? mc >> 1 : 0u) | (hi && b < 31 ? mc << 1 : 0u);
-                    const int ca = cr - 1 + py, cb = cr + py;          // cell rows of rows y - 1, y + 1
-                    const bool mv = moved != 0, va = mv && ca >= 0, vb = mv && cb < CRT;
-                    or_word(dirty, mv ? qrow * slot_words + cr * WPR + w : -1, mlr);
-                    or_word(dirty, va ? qcol * slot_words + ca * WPR + w : -1, mc);
-                    or_word(dirty, va ? qdiag * slot_words + ca * WPR + w : -1, mlr);
-                    or_word(dirty, vb ? qcol * slot_words + cb * WPR + w : -1, mc);
-                    or_word(dirty, vb ? qdiag * slot_words + cb * WPR + w : -1, mlr);
-                    if ((lo && b == 0) || (hi && b == 31)) {  // the group across a word boundary (rare)
-                        const int ws = lo && b == 0 ? w - 1 : w + 1;
-                        const uint32_t ms = lo && b == 0 ? 0x80000000u : 1u;
-                        atomicOr(&dirty[qrow * slot_words + cr * WPR + ws], ms);
-                        if (va) atomicOr(&dirty[qdiag * slot_words + ca * WPR + ws], ms);
-                        if (vb) atomicOr(&dirty[qdiag * slot_words + cb * WPR + ws], ms);
+                    const bool edge = px ? b == 31 : b == 0;  // the cell beside is in the next word
+                    const uint32_t mx = edge ? 0u : (px ? mc << 1 : mc >> 1);
+                    const uint32_t mrow = (rs ? mc : 0u) | (rx ? mx : 0u);
+                    const uint32_t ma = (as ? mc : 0u) | (ax ? mx : 0u);
+                    const uint32_t mb = (bs ? mc : 0u) | (bx ? mx : 0u);
+                    const int ca = cr - 1 + py, cb = cr + py;  // cell rows of rows y - 1, y + 1
+                    const bool va = ca >= 0, vb = cb < CRT;
+                    or_word(dirty, mrow ? qrow * slot_words + cr * WPR + w : -1, mrow);
+                    or_word(dirty, va && (A & 0x04040404u) ? qcol * slot_words + ca * WPR + w : -1, mc);
+                    or_word(dirty, va && ma ? qdiag * slot_words + ca * WPR + w : -1, ma);
+                    or_word(dirty, vb && (A & 0x40404040u) ? qcol * slot_words + cb * WPR + w : -1, mc);
+                    or_word(dirty, vb && mb ? qdiag * slot_words + cb * WPR + w : -1, mb);
+                    if (edge && (rx | ax | bx)) {  // the group across a word boundary (rare)
+                        const int ws = px ? w + 1 : w - 1;
+                        const uint32_t ms = px ? 1u : 0x80000000u;
+                        if (rx) atomicOr(&dirty[qrow * slot_words + cr * WPR + ws], ms);
+                        if (va && ax) atomicOr(&dirty[qdiag * slot_words + ca * WPR + ws], ms);
+                        if (vb && bx) atomicOr(&dirty[qdiag * slot_words + cb * WPR + ws], ms);
                     }
                 };
                 auto where = [&](int code, int &cr, int &cc, uint32_t &vm, uint32_t &in) {
@@ -422,21 +443,23 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                                    : test_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, J.lam, mode);
                     }
                 };
-                // the lowering loop on four points (ok: a first test's result, or ~0u to test first)
-                auto lower_item = [&](uint8_t *rb, int pxx, uint32_t vm, uint32_t in, uint32_t ok) -> uint32_t {
+                // the lowering loop on four points (ok: a first test's result, or ~0u to test first);
+                // aff receives the neighbours to mark
+                auto lower_item = [&](uint8_t *rb, int pxx, uint32_t vm, uint32_t in, uint32_t ok, uint32_t &aff) -> uint32_t {
                     if constexpr (ES == 1) {
                         if (ok == ~0u)
-                            return (kFix && mode == 0) ? item_u8<0>(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow)
-                                                       : item_u8(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow);
+                            return (kFix && mode == 0)
+                                       ? item_u8<0, kMark>(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow, aff, !wide)
+                                       : item_u8<-1, kMark>(rb - RP, rb, rb + RP, pxx, vm, in, J.lam, mode, nlow, aff, !wide);
                         return (kFix && mode == 0)
-                                   ? item_u8_tested<0>(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow)
-                                   : item_u8_tested(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow);
+                                   ? item_u8_tested<0, kMark>(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow, aff, !wide)
+                                   : item_u8_tested<-1, kMark>(rb - RP, rb, rb + RP, pxx, vm, in, ok, J.lam, mode, nlow, aff, !wide);
                     } else {
                         uint16_t *r16 = reinterpret_cast<uint16_t *>(rb);
                         const int rp16 = RP / 2;
                         return (kFix && mode == 0)
-                                   ? item_u16<0>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow)
-                                   : item_u16(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow);
+                                   ? item_u16<0, kMark>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow, aff, !wide)
+                                   : item_u16<-1, kMark>(r16 - rp16, r16, r16 + rp16, pxx, vm, in, ok, J.lam, mode, nlow, aff, !wide);
                     }
                 };
                 // A scan round: warp w takes the round's bitmap words 32 w .. 32 w + 31 of this parity
@@ -524,7 +547,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                         if (tmoved & in) moved_own = true;
                                     }
                                 }
-                                if (!simd) mark(gcr, gcc, tmoved);
+                                if (!simd) mark(gcr, gcc, tmoved * 0xffu);  // the table path marks every neighbour
                                 const unsigned bal = __ballot_sync(0xffffffffu, lowers);
                                 if (lowers) {
                                     const int at = nl + __popc(bal & ((1u << lane) - 1u));
@@ -540,7 +563,7 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                         for (int kb = 0; kb < nl; kb += 32) {
                             const int k = kb + lane;
                             int gcr = 0, gcc = 0;
-                            uint32_t moved = 0;
+                            uint32_t moved = 0, aff = 0;
                             if (k < nl) {
                                 const int code = wqueue[k];
                                 uint32_t vm, in;
@@ -550,13 +573,13 @@ __global__ void __launch_bounds__(NW * 32, kResMaxWarps / NW) k_resident(ResArgs
                                 if (kOkPass && nq > kTwoPass) {  // tested in the first pass: start lowering at once
                                     const uint32_t o4 = wok[k];
                                     const uint32_t okb = (o4 & 1u) | ((o4 & 2u) << 7) | ((o4 & 4u) << 14) | ((o4 & 8u) << 21);
-                                    moved = lower_item(rb, px, vm, in, okb);
+                                    moved = lower_item(rb, px, vm, in, okb, aff);
                                 } else {
-                                    moved = lower_item(rb, px, vm, in, ~0u);
+                                    moved = lower_item(rb, px, vm, in, ~0u, aff);
                                 }
                                 if (moved & in) moved_own = true;
                             }
-                            mark(gcr, gcc, moved);
+                            mark(gcr, gcc, aff);
                         }
                         __syncwarp();
                     }

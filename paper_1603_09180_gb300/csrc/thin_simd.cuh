@@ -78,14 +78,43 @@ __device__ __forceinline__ uint32_t lower_mask4(uint32_t c, const uint32_t nb[8]
     return merge_dirs(lt);
 }
 
+// Byte-wise arithmetic through 16-bit lanes.  The 16-bit lane minimum and
+// maximum are single instructions; their 4-byte forms are not (measured on
+// the GB300: __vmaxu4 and __vsubus4 cost about seven times __vmaxu2).  A word's
+// even bytes (mask 0x00ff00ff) and odd bytes (0xff00ff00), each left in
+// place, are two pairs of 16-bit lanes whose order is the bytes' order.
+constexpr uint32_t kEven8 = 0x00ff00ffu, kOdd8 = 0xff00ff00u;
+
+// c - l per byte, floored at 0.
+__device__ __forceinline__ uint32_t subus8(uint32_t c, uint32_t l)
+{
+    const uint32_t ce = c & kEven8, co = c & kOdd8;
+    return (ce - __vminu2(ce, l & kEven8)) | (co - __vminu2(co, l & kOdd8));
+}
+
+// c + l per byte, capped at 255: c + min(l, 255 - c), which stays in the lane.
+__device__ __forceinline__ uint32_t addus8(uint32_t c, uint32_t l)
+{
+    return ((c & kEven8) + __vminu2(l & kEven8, ~c & kEven8)) | ((c & kOdd8) + __vminu2(l & kOdd8, ~c & kOdd8));
+}
+
 // alpha^- of the four points given their lower masks M: the largest lower
-// neighbour, by a tree of byte maxima (0 where a mask is empty).
+// neighbour, by trees of maxima over the even and the odd bytes (0 where a
+// mask is empty).
 __device__ __forceinline__ uint32_t alpha4(const uint32_t nb[8], uint32_t M)
 {
-#define THIN_LOWER_NB(d) (nb[d] & ((((M >> (d)) & kLsb8) * 0xffu)))
-    return __vmaxu4(__vmaxu4(__vmaxu4(THIN_LOWER_NB(0), THIN_LOWER_NB(1)), __vmaxu4(THIN_LOWER_NB(2), THIN_LOWER_NB(3))),
-                    __vmaxu4(__vmaxu4(THIN_LOWER_NB(4), THIN_LOWER_NB(5)), __vmaxu4(THIN_LOWER_NB(6), THIN_LOWER_NB(7))));
-#undef THIN_LOWER_NB
+    uint32_t e[8], o[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const uint32_t v = nb[d] & (((M >> d) & kLsb8) * 0xffu);
+        e[d] = v & kEven8;
+        o[d] = v & kOdd8;
+    }
+    const uint32_t me = __vmaxu2(__vmaxu2(__vmaxu2(e[0], e[1]), __vmaxu2(e[2], e[3])),
+                                 __vmaxu2(__vmaxu2(e[4], e[5]), __vmaxu2(e[6], e[7])));
+    const uint32_t mo = __vmaxu2(__vmaxu2(__vmaxu2(o[0], o[1]), __vmaxu2(o[2], o[3])),
+                                 __vmaxu2(__vmaxu2(o[4], o[5]), __vmaxu2(o[6], o[7])));
+    return me | mo;
 }
 
 // Bit 7 set in each byte where a and b are equal.
@@ -171,7 +200,7 @@ __device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], u
 {
     return decide_masks<FIX>(M, vm, lam, mode_rt, [&] {
         const uint32_t lrep = (lam > 255u ? 255u : lam) * kLsb8;
-        const uint32_t cl = __vsubus4(c, lrep);
+        const uint32_t cl = subus8(c, lrep);
         const uint32_t cll = cl & 0x7f7f7f7fu, clh = cl & kMsb8;
         uint32_t dp[8];
 #pragma unroll
@@ -180,15 +209,47 @@ __device__ __forceinline__ uint32_t decide4m(uint32_t c, const uint32_t nb[8], u
     });
 }
 
+// Which neighbours of a lowered point must be tested again.  The test of a
+// neighbour q sees the point only through two bits: is it below F(q), and is
+// it below F(q) - lambda.  The point went from c0 down to c1, and no neighbour
+// lies strictly between two successive values of its lowering loop (each step
+// goes to the largest lower neighbour), so neither bit can change for a
+// neighbour q with F(q) <= c1 (the point stays >= F(q)), nor, for lambda-thinning,
+// with F(q) > c0 + lambda (the point was already below F(q) - lambda).  The
+// other neighbours are marked: byte k of the result holds the ring directions
+// of point k to mark (MARK 1: F(q) > c1; MARK 2: also F(q) <= c0 + lambda
+// where `cap` is set: the bound costs a compare per direction, which saves
+// more tests than it costs in a batch but not in the wide mode's tail).
+// Mlast: per moved point, its lower-neighbour mask before its last lowering
+// step, which is {F(q) <= c1}.  The decision of Sec. 2.1 depends on the
+// neighbour values only through those two masks, in both operators.
+template <int MARK>
+__device__ __forceinline__ uint32_t marks8(uint32_t okacc, uint32_t Mlast, uint32_t c0, const uint32_t nb[8], uint32_t lam,
+                                           bool cap)
+{
+    uint32_t aff = ~Mlast & (okacc * 0xffu);
+    if (MARK == 2 && cap && aff) {
+        const uint32_t t = addus8(c0, (lam > 255u ? 255u : lam) * kLsb8);  // c0 + lambda, saturated
+        uint32_t gt[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) gt[d] = lt8(t, nb[d], nb[d] & 0x7f7f7f7fu, nb[d] & kMsb8);
+        aff &= ~merge_dirs(gt);
+    }
+    return aff;
+}
+
 // The lowering loop of Sec. 2.2 on the four points: while a point is
 // lambda-destructible, F(x) := alpha^-(x, F), its neighbours fixed.  Returns
 // the bytes lowered (0x01 each) over all iterations; `c` receives the new
-// values, `nin` the lowering steps of the points also in `in`.
-template <int FIX = -1>
+// values, `nin` the lowering steps of the points also in `in`, `aff` the
+// neighbours to test again (marks8; every neighbour of a moved point when
+// MARK is 0).
+template <int FIX = -1, int MARK = 0>
 __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
-                                           uint32_t lam, int mode, int &nin)
+                                           uint32_t lam, int mode, int &nin, uint32_t &aff, bool cap = true)
 {
-    uint32_t okacc = 0;
+    uint32_t okacc = 0, Mlast = 0;
+    const uint32_t c0 = c;
     uint32_t M = lower_mask4(c, nb);
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
@@ -197,20 +258,24 @@ __device__ __forceinline__ uint32_t lower4(uint32_t &c, const uint32_t nb[8], ui
         const uint32_t alpha = alpha4(nb, M);
         const uint32_t okm = ok * 0xffu;
         c = (alpha & okm) | (c & ~okm);
+        if (MARK) Mlast = (M & okm) | (Mlast & ~okm);
         okacc |= ok;
         nin += __popc(ok & in);
         M &= ~equal_mask4(c, nb);  // unmoved points: no neighbour equal to c is lower
     }
+    aff = MARK ? marks8<MARK>(okacc, Mlast, c0, nb, lam, cap) : okacc * 0xffu;
     return okacc;
 }
 
 // lower4 for points whose first test already ran: `ok` holds its result
 // (0x01 per byte that may be lowered at the current values).
-template <int FIX = -1>
+template <int FIX = -1, int MARK = 0>
 __device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb[8], uint32_t vm, uint32_t in,
-                                                  uint32_t ok, uint32_t lam, int mode, int &nin)
+                                                  uint32_t ok, uint32_t lam, int mode, int &nin, uint32_t &aff,
+                                                  bool cap = true)
 {
-    uint32_t okacc = 0;
+    uint32_t okacc = 0, Mlast = 0;
+    const uint32_t c0 = c;
     uint32_t M = lower_mask4(c, nb);
 #pragma unroll 1
     for (int it = 0; it < 9; ++it) {
@@ -218,11 +283,13 @@ __device__ __forceinline__ uint32_t lower4_tested(uint32_t &c, const uint32_t nb
         const uint32_t alpha = alpha4(nb, M);
         const uint32_t okm = ok * 0xffu;
         c = (alpha & okm) | (c & ~okm);
+        if (MARK) Mlast = (M & okm) | (Mlast & ~okm);
         okacc |= ok;
         nin += __popc(ok & in);
         M &= ~equal_mask4(c, nb);
         ok = decide4m<FIX>(c, nb, vm, lam, mode, M);
     }
+    aff = MARK ? marks8<MARK>(okacc, Mlast, c0, nb, lam, cap) : okacc * 0xffu;
     return okacc;
 }
 
@@ -281,13 +348,14 @@ __device__ __forceinline__ uint32_t test_u8(const uint8_t *ra, const uint8_t *rb
 }
 
 // One u8 work item, lowered: the lowering loop on its four points, the block written back.
-template <int FIX = -1>
+// aff: the neighbours to test again (lower4).
+template <int FIX = -1, int MARK = 0>
 __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px, uint32_t vm,
-                                            uint32_t in, uint32_t lam, int mode, int &nin)
+                                            uint32_t in, uint32_t lam, int mode, int &nin, uint32_t &aff, bool cap = true)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4<FIX>(c, nb, vm, in, lam, mode, nin);
+    const uint32_t moved = lower4<FIX, MARK>(c, nb, vm, in, lam, mode, nin, aff, cap);
     if (moved) {
         uint2 out;
         if (px == 0)
@@ -300,13 +368,14 @@ __device__ __forceinline__ uint32_t item_u8(const uint8_t *ra, uint8_t *rb, cons
 }
 
 // item_u8 for a work item whose first test already ran (result `ok`).
-template <int FIX = -1>
+template <int FIX = -1, int MARK = 0>
 __device__ __forceinline__ uint32_t item_u8_tested(const uint8_t *ra, uint8_t *rb, const uint8_t *rc, int px,
-                                                   uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin)
+                                                   uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin,
+                                                   uint32_t &aff, bool cap = true)
 {
     uint32_t nb[8], c, other;
     gather_u8(ra, rb, rc, px, nb, c, other);
-    const uint32_t moved = lower4_tested<FIX>(c, nb, vm, in, ok, lam, mode, nin);
+    const uint32_t moved = lower4_tested<FIX, MARK>(c, nb, vm, in, ok, lam, mode, nin, aff, cap);
     if (moved) {
         uint2 out;
         if (px == 0)
@@ -419,17 +488,39 @@ __device__ __forceinline__ uint32_t decide16m(const Px16 &P, uint32_t vm, uint32
 {
     return decide_masks<FIX>(M, vm, lam, mode, [&] {
         const uint32_t lrep = (lam > 65535u ? 65535u : lam) * 0x00010001u;
-        return lower_mask16(P, __vsubus2(P.cA, lrep), __vsubus2(P.cB, lrep));
+        // c - lambda per lane, floored at 0
+        return lower_mask16(P, P.cA - __vminu2(P.cA, lrep), P.cB - __vminu2(P.cB, lrep));
     });
+}
+
+// marks8 for u16 items (c0A, c0B: the values before the lowering loop).
+template <int MARK>
+__device__ __forceinline__ uint32_t marks16(const Px16 &P, uint32_t okacc, uint32_t Mlast, uint32_t c0A, uint32_t c0B,
+                                            uint32_t lam, bool cap)
+{
+    uint32_t aff = ~Mlast & (okacc * 0xffu);
+    if (MARK == 2 && cap && aff) {
+        const uint32_t lrep = (lam > 65535u ? 65535u : lam) * 0x00010001u;
+        // c0 + lambda per lane, capped at 65535: c0 + min(lambda, 65535 - c0)
+        const uint32_t tA = c0A + __vminu2(lrep, ~c0A), tB = c0B + __vminu2(lrep, ~c0B);
+        uint32_t gt[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) gt[d] = lanes_to_bytes(lt16(tA, P.nbA[d]), lt16(tB, P.nbB[d]));
+        aff &= ~merge_dirs(gt);
+    }
+    return aff;
 }
 
 // The lowering loop on the four points (u16).  ok: the result of a first test
 // already made at the current values, or ~0u to test first.  Returns the bytes
-// lowered (0x01 each); P.cA, P.cB receive the new values.
-template <int FIX>
-__device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin)
+// lowered (0x01 each); P.cA, P.cB receive the new values, aff the neighbours
+// to test again (marks16; every neighbour of a moved point when MARK is 0).
+template <int FIX, int MARK = 0>
+__device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, uint32_t ok, uint32_t lam, int mode, int &nin,
+                                            uint32_t &aff, bool cap = true)
 {
-    uint32_t okacc = 0;
+    uint32_t okacc = 0, Mlast = 0;
+    const uint32_t c0A = P.cA, c0B = P.cB;
     uint32_t M = lower_mask16(P, P.cA, P.cB);
     if (ok == ~0u) ok = decide16m<FIX>(P, vm, lam, mode, M);
 #pragma unroll 1
@@ -440,11 +531,16 @@ __device__ __forceinline__ uint32_t lower16(Px16 &P, uint32_t vm, uint32_t in, u
         const uint32_t mA = lanes_of_bytes_lo(ok), mB = lanes_of_bytes_hi(ok);
         P.cA = (aA & mA) | (P.cA & ~mA);
         P.cB = (aB & mB) | (P.cB & ~mB);
+        if (MARK) {
+            const uint32_t okm = ok * 0xffu;
+            Mlast = (M & okm) | (Mlast & ~okm);
+        }
         okacc |= ok;
         nin += __popc(ok & in);
         M &= ~equal_mask16(P);  // unmoved points: no neighbour equal to c is lower
         ok = decide16m<FIX>(P, vm, lam, mode, M);
     }
+    aff = MARK ? marks16<MARK>(P, okacc, Mlast, c0A, c0B, lam, cap) : okacc * 0xffu;
     return okacc;
 }
 
@@ -524,16 +620,16 @@ __device__ __forceinline__ uint32_t test_u16(const uint16_t *ra, const uint16_t 
 }
 
 // One u16 work item under (8,4), lowered (ok: a first test's result, or ~0u);
-// the block is written back if a point moved.
-template <int FIX = -1>
+// the block is written back if a point moved.  aff: the neighbours to test again.
+template <int FIX = -1, int MARK = 0>
 __device__ __forceinline__ uint32_t item_u16(const uint16_t *ra, uint16_t *rb, const uint16_t *rc, int px, uint32_t vm,
                                              uint32_t in, uint32_t ok, uint32_t lam, int mode,
-                                             int &nin)
+                                             int &nin, uint32_t &aff, bool cap = true)
 {
     Px16 P;
     uint4 w;
     gather_u16(ra, rb, rc, px, P, w);
-    const uint32_t moved = lower16<FIX>(P, vm, in, ok, lam, mode, nin);
+    const uint32_t moved = lower16<FIX, MARK>(P, vm, in, ok, lam, mode, nin, aff, cap);
     if (moved) store_u16(rb, px, P, w);
     return moved;
 }

@@ -303,16 +303,16 @@ __device__ void visit_phases(T *tile, int bw, int32_t *cells, int ccols, uint16_
             const bool inside = unsigned(sr - V.hr) < unsigned(V.th) && sb >= V.pad && sb < V.pad + V.tw;
             const uint32_t in = inside ? vm : 0u;
             ntest += __popc(in);
-            uint32_t moved;
+            uint32_t moved, aff;  // (this engine marks whole cells: aff is not used)
             T *rb = tile + sr * bw + sb;
             if (sizeof(T) == 1 && !(V.rule & 4))  // u8 under (8,4): four points at once
                 moved = item_u8(reinterpret_cast<const uint8_t *>(rb - bw), reinterpret_cast<uint8_t *>(rb),
                                 reinterpret_cast<const uint8_t *>(rb + bw), px, vm, in, V.lam, V.rule,
-                                nlow);
+                                nlow, aff);
             else if (sizeof(T) == 2 && !(V.rule & 4))  // u16 under (8,4): four points in 16-bit lanes
                 moved = item_u16(reinterpret_cast<const uint16_t *>(rb - bw), reinterpret_cast<uint16_t *>(rb),
                                  reinterpret_cast<const uint16_t *>(rb + bw), px, vm, in, ~0u, V.lam,
-                                 V.rule, nlow);
+                                 V.rule, nlow, aff);
             else
                 moved = item_table<T>(rb - bw, rb, rb + bw, px, vm, in, tabs + ((V.rule & 4) ? kTabOffset48 : 0), V.lam,
                                       V.rule, nlow);
