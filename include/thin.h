@@ -301,14 +301,14 @@ const char *thin_version(void);
  * shared memory (the resident engine), and larger ones (the tiled engine).
  * An idle lane admits requests of one queue in arrival order while the slot
  * count and the byte budget allow, at most max_slots / 8 of them (a request
- * that does not fit waits at the head of its queue); one lane at a time
- * takes from the large queue, and its tiled launch uses at most half of the
- * SMs, so small requests keep running beside it.  The lane allocates the
- * device images, copies them in and launches them as one batch (never the
- * wide mode, so that the lanes share the GPU).  Each resident image is
- * retired as soon as it is finished -- its result copied back and its bytes
- * and slot returned -- while the rest of its batch still runs; tiled images
- * retire when their batch ends.  Queued requests are
+ * that does not fit waits at the head of its queue); at most two lanes at a
+ * time take from the large queue, and each of their tiled launches uses at
+ * most a quarter of the SMs, so small requests keep running beside them.
+ * The lane allocates the device images, copies them in and launches them as
+ * one batch (never the wide mode, so that the lanes share the GPU).  Each
+ * resident image is retired as soon as it is finished -- its result copied
+ * back and its bytes and slot returned -- while the rest of its batch still
+ * runs; tiled images retire when their batch ends.  Queued requests are
  * admitted by the next idle lane as slots and memory free up, and run on the
  * device beside the batches already there.  Host staging is one pinned arena
  * allocated at create (a quarter of the device budget, clamped to

@@ -11,9 +11,13 @@
 // retires the request at once, returning its bytes and slot while the rest
 // of the batch still runs, so queued requests are admitted by the next idle
 // lane as slots and memory free up.  Images too large for a cluster wait in
-// a queue of their own; one lane at a time runs a batch of them on the tiled
-// engine, on at most half of the SMs, and they retire when that batch ends.
-// So small requests keep flowing on the other SMs while a large one runs.
+// a queue of their own; at most two lanes at a time run a batch of them on
+// the tiled engine, each on at most a quarter of the SMs, and they retire
+// when their batch ends.  So small requests keep flowing on the other SMs
+// while large ones run.  (The tiled launch is cooperative: it starts only
+// when all its blocks fit at once.  Capped at half of the SMs it waited for
+// the long resident jobs to drain, and the small launches queued behind it;
+// two quarter-size launches start sooner and keep the same share.)
 // Lanes run side by side on the device (the resident engine gives each image
 // its own cluster and takes only the SMs it needs).  Each image's result depends
 // only on the image and its lambda: it is the same alone and in any mix.
@@ -36,6 +40,7 @@ namespace thin {
 namespace {
 
 constexpr int kLanes = 8;          // batches in flight at once
+constexpr int kLargeLanes = 2;     // of which batches of large (tiled-engine) requests
 constexpr int kMaxBatch = 512;     // requests one lane admits at a time
 
 enum ReqState { kQueued, kRunning, kDone };
@@ -129,7 +134,7 @@ struct thin_server {
     std::condition_variable cv;
     std::deque<thin::Req *> queue;        // requests that fit a cluster (the resident engine)
     std::deque<thin::Req *> queue_large;  // the rest (the tiled engine)
-    bool large_busy = false;              // a lane is running a batch of large requests
+    int large_running = 0;                // lanes running a batch of large requests (kLargeLanes at most)
     size_t res_smem_limit = 0;            // a resident block's shared memory (one block per SM)
     std::unordered_map<uint64_t, thin::Req *> reqs;
     std::deque<uint64_t> finished;  // tickets in the order they finished, for thin_serve_wait_any
@@ -195,11 +200,11 @@ void lane_main(thin_server *S)
         cudaGetLastError();
         ok_lane = false;
     }
-    // a large batch's tiled launch takes at most half of the SMs, so that the resident
-    // launches of the other lanes keep running beside it
+    // a large batch's tiled launch takes at most a quarter of the SMs (two may run), so that
+    // the resident launches of the other lanes keep running beside them
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
-    const int tiled_cap = std::max(1, sms / 2);
+    const int tiled_cap = std::max(1, sms / (2 * kLargeLanes));
     std::vector<Req *> batch;
     for (;;) {
         batch.clear();
@@ -213,11 +218,11 @@ void lane_main(thin_server *S)
             S->cv.wait(g, [&] {
                 if (S->stop) return true;
                 if (S->in_flight >= S->max_slots) return false;
-                return fits(S->queue) || (!S->large_busy && fits(S->queue_large));
+                return fits(S->queue) || (S->large_running < kLargeLanes && fits(S->queue_large));
             });
             if (S->stop) break;
-            large = !S->large_busy && fits(S->queue_large);
-            if (large) S->large_busy = true;
+            large = S->large_running < kLargeLanes && fits(S->queue_large);
+            if (large) ++S->large_running;
             std::deque<Req *> &q = large ? S->queue_large : S->queue;
             // a lane takes at most its share of the slots, so that under load the other lanes
             // keep admitting while this lane's batch runs
@@ -231,7 +236,7 @@ void lane_main(thin_server *S)
                 r->state = kRunning;
                 batch.push_back(r);
             }
-            if (batch.empty() && large) S->large_busy = false;
+            if (batch.empty() && large) --S->large_running;
         }
         if (batch.empty()) continue;
         NvtxRange nv("thin_serve batch");
@@ -346,7 +351,7 @@ void lane_main(thin_server *S)
         if (large) {
             {
                 std::lock_guard<std::mutex> g(S->mu);
-                S->large_busy = false;
+                --S->large_running;
             }
             S->cv.notify_all();
         }
