@@ -50,7 +50,7 @@ extern "C" {
 
 #define THIN_OK 0
 #define THIN_ERR_ARG (-1)           /* bad pointer, size, pitch, dtype, lambda or option */
-#define THIN_ERR_UNSUPPORTED (-2)   /* an option this build lacks */
+#define THIN_ERR_UNSUPPORTED (-2)   /* an option the library was compiled without */
 #define THIN_ERR_OOM (-3)           /* scratch allocation failed */
 #define THIN_ERR_NOT_CONVERGED (-4) /* stopped by max_phases before stability */
 #define THIN_ERR_TIMEOUT (-5)       /* a bounded device wait ran out */
