@@ -357,6 +357,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         if k:  # first one is a warm-up
             e2e_serial_ms.append(e0.elapsed_time(e1))
 
+    # the paper's own operator, the lambda-skeleton (Sec. 2.2), on the same 192 jobs: the figure that
+    # compares one to one with the paper's 125 images/s (outside the timed steps; `value` stays lambda-thinning)
+    plan_sk = thin.BatchPlan([work[k] for k in range(n_jobs)], lams, op="skeleton", **opts)
+    with ClockSampler(local_rank) as clk_k:
+        ms_sk = statistics.median(_timed(lambda: plan_sk.run(stream), lambda: work.copy_(pristine), flush, stream, 5, 3))
+    skeleton = {"images_per_s": round(n_jobs / (ms_sk / 1e3), 1), "ms_per_step": round(ms_sk, 4), "steps": 5,
+                "warmup": 3, "x_paper": round(n_jobs / (ms_sk / 1e3) / PAPER_IMG_PER_S, 1), "clocks": clk_k.summary(),
+                "note": "the same 192 jobs under the lambda-skeleton (lambda-deletable and not lambda-end), one "
+                        "thin_batch call per step, L2 flushed before each; median of 5"}
+
     # the other two parts of the metric: large single images (Gpix-sweeps/s against the HBM roofline) and
     # serving (images/s and p50/p99 latency below and at capacity)
     large = serve = None
@@ -444,6 +454,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                     "max": round(max(step_ms), 4)},
         "rounds": rounds_profile(sts),
         "engine": args.kernel,
+        "skeleton": skeleton,
         "large": large,
         "serve": serve,
     }
